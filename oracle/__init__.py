@@ -1,0 +1,143 @@
+"""CPU oracle for second-eye synthesis: numpy front end over ``yoro_oracle.c``.
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this package.  The product library
+does not import, link or call anything here, and nothing here imports the product.
+
+Each function mirrors one step of the method (Algorithm 1 closed form, Algorithm 2
+nearest-wins write, the gather, disocclusion edges, Algorithm 3 with Eq. 6); see
+the C source for the definitions and the paper passages they follow.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "yoro_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+# binary32 semantics: no contraction of a*b+c into an FMA, no fast-math reassociation.
+CFLAGS = ["-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fexcess-precision=standard"]
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into ``oracle/liboracle.so``."""
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", *CFLAGS, "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        # YORO_ORACLE_LIB names a separately built copy (used by the mutation test).
+        lib = ctypes.CDLL(os.environ.get("YORO_ORACLE_LIB") or build())
+        P = ctypes.c_void_p
+        I, F = ctypes.c_int, ctypes.c_float
+        lib.oracle_disparity.argtypes = [I, I, F, F, F, F, P, P, P]
+        lib.oracle_disparity.restype = None
+        lib.oracle_forward_warp.argtypes = [I, I, P, P, P, P]
+        lib.oracle_forward_warp.restype = None
+        lib.oracle_resolve.argtypes = [I, I, P, P, P, P]
+        lib.oracle_resolve.restype = None
+        lib.oracle_hole_edges.argtypes = [I, I, P, P, P]
+        lib.oracle_hole_edges.restype = None
+        lib.oracle_fill.argtypes = [I, I, P, P, P, P, P, P]
+        lib.oracle_fill.restype = None
+        lib.oracle_synthesize.argtypes = [I, I, F, F, F, F, F, F, F, P, P, P, P]
+        lib.oracle_synthesize.restype = I
+        _lib = lib
+    return _lib
+
+
+def _c(a, dtype):
+    a = np.ascontiguousarray(a, dtype=dtype)
+    return a
+
+
+def disparity(depth, fx, ipd, near, far):
+    """Algorithm 1 closed form: (xt int32[H,W] with -1 = off frame, zc float32[H,W])."""
+    depth = _c(depth, np.float32)
+    h, w = depth.shape
+    xt = np.empty((h, w), np.int32)
+    zc = np.empty((h, w), np.float32)
+    _load().oracle_disparity(w, h, fx, ipd, near, far, depth.ctypes.data, xt.ctypes.data, zc.ctypes.data)
+    return xt, zc
+
+
+def forward_warp(xt, zc):
+    """Algorithm 2 nearest-wins write: (src int32[H,W] with -1 = hole, zt float32[H,W])."""
+    xt = _c(xt, np.int32)
+    zc = _c(zc, np.float32)
+    h, w = xt.shape
+    src = np.empty((h, w), np.int32)
+    zt = np.empty((h, w), np.float32)
+    _load().oracle_forward_warp(w, h, xt.ctypes.data, zc.ctypes.data, src.ctypes.data, zt.ctypes.data)
+    return src, zt
+
+
+def resolve(color, src):
+    """Gather: (warped uint8[H,W,4] with holes zeroed, mask uint8[H,W] with 1 = hole)."""
+    color = _c(color, np.uint8)
+    src = _c(src, np.int32)
+    h, w = src.shape
+    warped = np.empty((h, w, 4), np.uint8)
+    mask = np.empty((h, w), np.uint8)
+    _load().oracle_resolve(w, h, color.ctypes.data, src.ctypes.data, warped.ctypes.data, mask.ctypes.data)
+    return warped, mask
+
+
+def hole_edges(src):
+    """Nearest reached column left (L, -1 if none) and right (R, W if none) of each hole."""
+    src = _c(src, np.int32)
+    h, w = src.shape
+    L = np.empty((h, w), np.int32)
+    R = np.empty((h, w), np.int32)
+    _load().oracle_hole_edges(w, h, src.ctypes.data, L.ctypes.data, R.ctypes.data)
+    return L, R
+
+
+def fill(src, zt, L, R, warped):
+    """Algorithm 3 + Eq. 6 over every hole pixel: the final uint8[H,W,4] image."""
+    src = _c(src, np.int32)
+    zt = _c(zt, np.float32)
+    L = _c(L, np.int32)
+    R = _c(R, np.int32)
+    warped = _c(warped, np.uint8)
+    h, w = src.shape
+    out = np.empty((h, w, 4), np.uint8)
+    _load().oracle_fill(w, h, src.ctypes.data, zt.ctypes.data, L.ctypes.data, R.ctypes.data,
+                        warped.ctypes.data, out.ctypes.data)
+    return out
+
+
+def synthesize(color, depth, fx, fy, cx, cy, ipd, near, far):
+    """Left eye (color uint8[H,W,4], depth float32[H,W]) -> right eye (color, hole mask)."""
+    color = _c(color, np.uint8)
+    depth = _c(depth, np.float32)
+    h, w = depth.shape
+    if color.shape != (h, w, 4):
+        raise ValueError("color must be uint8[H,W,4] matching depth")
+    out = np.empty((h, w, 4), np.uint8)
+    mask = np.empty((h, w), np.uint8)
+    rc = _load().oracle_synthesize(w, h, fx, fy, cx, cy, ipd, near, far, color.ctypes.data,
+                                   depth.ctypes.data, out.ctypes.data, mask.ctypes.data)
+    if rc != 0:
+        raise RuntimeError(f"oracle_synthesize failed ({rc})")
+    return out, mask
+
+
+def synthesize_steps(color, depth, fx, ipd, near, far):
+    """The path step by step, returning every intermediate (for tests)."""
+    xt, zc = disparity(depth, fx, ipd, near, far)
+    src, zt = forward_warp(xt, zc)
+    warped, mask = resolve(color, src)
+    L, R = hole_edges(src)
+    out = fill(src, zt, L, R, warped)
+    return dict(xt=xt, zc=zc, src=src, zt=zt, warped=warped, mask=mask, L=L, R=R, out=out)

@@ -1,0 +1,298 @@
+/*
+ * CPU oracle for second-eye synthesis (YORO, "You Only Render Once").
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the CPU
+ * baseline of the benchmark load this file.  The CUDA library never includes,
+ * links or calls it, and it shares no header, helper or constant table with it.
+ *
+ * Plain, slow and sequential on purpose: every step is the paper's definition
+ * written out in the order the paper gives, so it can be checked against the
+ * paper by eye.  Compiled with -O2 -ffp-contract=off and no fast-math, so every
+ * float operation below is one IEEE binary32 operation rounded to nearest even.
+ *
+ * Precision: binary32 throughout.  The method turns floating point into integers
+ * (a target column, a winning source, an 8-bit color), and those decisions are
+ * taken in the precision of the CUDA path so that both sides agree exactly.
+ *
+ * Frame convention: the source is the LEFT eye and the output is the RIGHT eye.
+ * The paper's examples use the right eye as source (pixels move +x, background at
+ * -x); here pixels move -x and the background side of a hole is +x, so every
+ * left/right choice of the paper is mirrored.
+ *
+ * Pins (tests that tie this file to the paper and to mathematics, not to itself):
+ *   oracle_disparity     IPD = 0 identity; fronto-parallel plane closed-form shift;
+ *                        analytic ray-cast of the right eye on tiny scenes.
+ *   oracle_forward_warp  brute-force argmin over co-mapped sources (nearer wins,
+ *                        lower source column on equal depth); ray-cast visibility.
+ *   oracle_resolve       IPD = 0 identity; plane closed form.
+ *   oracle_hole_edges    brute force nearest valid column on each side.
+ *   oracle_fill          closed forms: one contributing candidate returns its color;
+ *                        two contributors blend as c2 + (c1 - c2) / (1.5 - 0.3 t);
+ *                        depth gate, kernel extent, row order and the fallback are
+ *                        checked by hand-built cases.  Beyond those small cases the
+ *                        fill on general inputs is parity unpinned: it follows the
+ *                        literal reading of Algorithm 3 and Eq. 6 stated below.
+ */
+#include <math.h>
+#include <stddef.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/*
+ * Algorithm 1 (Reprojector stage 1) in closed form, per source pixel (y, x).
+ *
+ * Eq. 5 maps a source pixel to the other eye with M = (VP_left)^-1 VP_right.  For
+ * two pinhole eyes with the same intrinsics, parallel axes and a baseline of ipd
+ * along +x, back-projecting pixel centre x + 0.5 at depth z gives
+ * X = (x + 0.5 - cx) z / fx, and projecting into the eye at +ipd gives
+ * x_R + 0.5 = fx (X - ipd) / z + cx = (x + 0.5) - fx ipd / z, with y and z
+ * unchanged (observation O1: motion is along x only, in one direction).
+ *
+ *   k    = fx * ipd                          (once per frame)
+ *   z    = depth, or far if depth is not a positive finite number
+ *   zc   = min(max(z, near), far)            (the camera's near/far planes, Eq. 3)
+ *   disp = k / zc
+ *   t    = (x + 0.5) - disp
+ *   xt   = floor(t)                          (the target pixel whose cell holds t)
+ *
+ * xt[y*w+x] receives the target column, or -1 if it falls outside [0, w).
+ * zc[y*w+x] receives the clamped depth.
+ */
+void oracle_disparity(int w, int h, float fx, float ipd, float near_, float far_,
+                      const float* depth, int32_t* xt, float* zc)
+{
+    const float k = fx * ipd;
+    for (int y = 0; y < h; ++y) {
+        for (int x = 0; x < w; ++x) {
+            size_t i = (size_t)y * (size_t)w + (size_t)x;
+            float z = depth[i];
+            if (!(z > 0.0f) || isinf(z)) z = far_;
+            float c = fminf(fmaxf(z, near_), far_);
+            float disp = k / c;
+            float t = ((float)x + 0.5f) - disp;
+            float f = floorf(t);
+            xt[i] = (f >= 0.0f && f < (float)w) ? (int32_t)f : -1;
+            zc[i] = c;
+        }
+    }
+}
+
+/*
+ * Algorithm 2 (Reprojector stage 2), the write with the nearest kept.
+ *
+ * Each row is scanned left to right, as the per-row compute shader does; a source
+ * pixel overwrites its target only if it is strictly nearer than what is there, so
+ * on equal depth the first (lowest) source column keeps the target.  Smaller depth
+ * is nearer (linear view-space z).
+ *
+ * The paper's scan also writes hole records into skipped pixels while it runs,
+ * which makes the result depend on the scan order; here a hole is simply a target
+ * that no source reaches, and its edges are found afterwards (oracle_hole_edges).
+ *
+ * src[y*w+u] receives the winning source column (same row, O1) or -1 for a hole;
+ * zt[y*w+u] receives the winner's clamped depth, or +inf for a hole.
+ */
+void oracle_forward_warp(int w, int h, const int32_t* xt, const float* zc, int32_t* src, float* zt)
+{
+    for (int y = 0; y < h; ++y) {
+        for (int u = 0; u < w; ++u) {
+            size_t i = (size_t)y * (size_t)w + (size_t)u;
+            src[i] = -1;
+            zt[i] = INFINITY;
+        }
+        for (int x = 0; x < w; ++x) {
+            size_t i = (size_t)y * (size_t)w + (size_t)x;
+            int t = xt[i];
+            if (t < 0) continue;
+            size_t o = (size_t)y * (size_t)w + (size_t)t;
+            if (src[o] < 0 || zc[i] < zt[o]) {
+                src[o] = x;
+                zt[o] = zc[i];
+            }
+        }
+    }
+}
+
+/*
+ * Gather (Algorithm 3, non-hole branch): a reached target takes the source color of
+ * the pixel that won it, all four bytes (alpha is carried like a color channel).
+ * mask = 0 for reached targets and 1 for holes (disocclusions).  Hole pixels of
+ * out_color are set to 0 here and written by oracle_fill.
+ */
+void oracle_resolve(int w, int h, const uint8_t* color, const int32_t* src, uint8_t* out_color,
+                    uint8_t* mask)
+{
+    for (int y = 0; y < h; ++y) {
+        for (int u = 0; u < w; ++u) {
+            size_t i = (size_t)y * (size_t)w + (size_t)u;
+            if (src[i] >= 0) {
+                size_t s = (size_t)y * (size_t)w + (size_t)src[i];
+                memcpy(out_color + 4 * i, color + 4 * s, 4);
+                mask[i] = 0;
+            } else {
+                memset(out_color + 4 * i, 0, 4);
+                mask[i] = 1;
+            }
+        }
+    }
+}
+
+/*
+ * Disocclusion tracking (strategy (b)): for every hole pixel u of row y, the nearest
+ * reached column on each side.  L = largest reached x < u (or -1), R = smallest
+ * reached x > u (or w).  For reached pixels both are set to u.  In this frame L is
+ * the occluder (foreground) side and R the background side of the hole; the hole
+ * width of Algorithm 2 (target-column jump, edge to edge) is R - L.
+ */
+void oracle_hole_edges(int w, int h, const int32_t* src, int32_t* L, int32_t* R)
+{
+    for (int y = 0; y < h; ++y) {
+        const int32_t* s = src + (size_t)y * (size_t)w;
+        for (int u = 0; u < w; ++u) {
+            size_t i = (size_t)y * (size_t)w + (size_t)u;
+            if (s[u] >= 0) {
+                L[i] = u;
+                R[i] = u;
+                continue;
+            }
+            int l = u - 1;
+            while (l >= 0 && s[l] < 0) --l;
+            int r = u + 1;
+            while (r < w && s[r] < 0) ++r;
+            L[i] = l;
+            R[i] = r;
+        }
+    }
+}
+
+/*
+ * Patcher (Algorithm 3 with the weight of Eq. 6) for one hole pixel (v, u).
+ *
+ * Reading used (paper mirrored to a left-eye source):
+ *   w      = R - L                       hole width of Algorithm 2
+ *   d_occ  = zt(v, L), or 0 if L = -1    depth of the occluding edge
+ *   t      = (R - u) / w                 Eq. 6's (u - r_x) / r_z, distance from the
+ *                                        background edge over the hole width
+ *   kernel = rows v-1, v, v+1 (h = 3, rows outside the image skipped), and in each
+ *            row the w + 1 columns from min(R + w, w_img - 1) down to R: the
+ *            background side, farthest column first, as Algorithm 3's kernel runs
+ *            from r.x - r.z up to r.x in the paper's frame.
+ *   A candidate is skipped if it is a hole (it carries no color) or if it is
+ *   strictly nearer than d_occ (a foreground pixel, observation O2).  Otherwise:
+ *       wgt   = wrem / 2 + 0.3 wrem t   (Eq. 6, evaluated as (wrem * 0.5) +
+ *                                        ((0.3 * wrem) * t), each step rounded)
+ *       acc   = acc + C[j] * wgt         (per channel, multiply then add)
+ *       wrem  = wrem - wgt
+ *   Result: acc / (1 - wrem) per channel, rounded half to even and clamped to
+ *   [0, 255].
+ *   Fallback (no background edge, R = w_img, or no candidate contributed): copy the
+ *   warped color at (v, R) if R < w_img, else at (v, L) if L >= 0, else zero.
+ */
+static void fill_one(int w, int h, int v, int u, int L, int R, const int32_t* src, const float* zt,
+                     const uint8_t* warped, uint8_t out[4])
+{
+    if (R < w) {
+        int wd = R - L;
+        float d_occ = (L >= 0) ? zt[(size_t)v * (size_t)w + (size_t)L] : 0.0f;
+        float t = (float)(R - u) / (float)wd;
+        float acc[4] = { 0.0f, 0.0f, 0.0f, 0.0f };
+        float wrem = 1.0f;
+        for (int vv = v - 1; vv <= v + 1; ++vv) {
+            if (vv < 0 || vv >= h) continue;
+            int jhi = R + wd;
+            if (jhi > w - 1) jhi = w - 1;
+            for (int j = jhi; j >= R; --j) {
+                size_t q = (size_t)vv * (size_t)w + (size_t)j;
+                if (src[q] < 0) continue;
+                if (zt[q] < d_occ) continue;
+                float a = wrem * 0.5f;
+                float b = (0.3f * wrem) * t;
+                float wgt = a + b;
+                for (int c = 0; c < 4; ++c) {
+                    float term = (float)warped[4 * q + c] * wgt;
+                    acc[c] = acc[c] + term;
+                }
+                wrem = wrem - wgt;
+            }
+        }
+        if (wrem != 1.0f) {
+            float den = 1.0f - wrem;
+            for (int c = 0; c < 4; ++c) {
+                float r = rintf(acc[c] / den);
+                if (r < 0.0f) r = 0.0f;
+                if (r > 255.0f) r = 255.0f;
+                out[c] = (uint8_t)r;
+            }
+            return;
+        }
+    }
+    if (R < w)
+        memcpy(out, warped + 4 * ((size_t)v * (size_t)w + (size_t)R), 4);
+    else if (L >= 0)
+        memcpy(out, warped + 4 * ((size_t)v * (size_t)w + (size_t)L), 4);
+    else
+        memset(out, 0, 4);
+}
+
+/*
+ * Fill every hole pixel (mask = 1) of `warped` (the resolved image) into out_color;
+ * reached pixels are copied unchanged.  Candidates are read from `warped` only.
+ */
+void oracle_fill(int w, int h, const int32_t* src, const float* zt, const int32_t* L, const int32_t* R,
+                 const uint8_t* warped, uint8_t* out_color)
+{
+    for (int v = 0; v < h; ++v) {
+        for (int u = 0; u < w; ++u) {
+            size_t i = (size_t)v * (size_t)w + (size_t)u;
+            if (src[i] >= 0) {
+                memcpy(out_color + 4 * i, warped + 4 * i, 4);
+                continue;
+            }
+            fill_one(w, h, v, u, L[i], R[i], src, zt, warped, out_color + 4 * i);
+        }
+    }
+}
+
+/*
+ * The whole path, left eye -> right eye.  fy, cx and cy are accepted for the
+ * camera description but do not enter the result: for a parallel-axis pair with
+ * shared intrinsics the vertical coordinate is unchanged and cx cancels.
+ * Returns 0, -1 on bad sizes, -2 if a temporary could not be allocated.
+ */
+int oracle_synthesize(int w, int h, float fx, float fy, float cx, float cy, float ipd, float near_,
+                      float far_, const uint8_t* color, const float* depth, uint8_t* out_color,
+                      uint8_t* mask)
+{
+    (void)fy;
+    (void)cx;
+    (void)cy;
+    if (w < 0 || h < 0) return -1;
+    size_t n = (size_t)w * (size_t)h;
+    if (n == 0) return 0;
+    int32_t* xt = (int32_t*)malloc(n * sizeof(int32_t));
+    float* zc = (float*)malloc(n * sizeof(float));
+    int32_t* src = (int32_t*)malloc(n * sizeof(int32_t));
+    float* zt = (float*)malloc(n * sizeof(float));
+    int32_t* L = (int32_t*)malloc(n * sizeof(int32_t));
+    int32_t* R = (int32_t*)malloc(n * sizeof(int32_t));
+    uint8_t* warped = (uint8_t*)malloc(n * 4);
+    int rc = 0;
+    if (!xt || !zc || !src || !zt || !L || !R || !warped) {
+        rc = -2;
+    } else {
+        oracle_disparity(w, h, fx, ipd, near_, far_, depth, xt, zc);
+        oracle_forward_warp(w, h, xt, zc, src, zt);
+        oracle_resolve(w, h, color, src, warped, mask);
+        oracle_hole_edges(w, h, src, L, R);
+        oracle_fill(w, h, src, zt, L, R, warped, out_color);
+    }
+    free(xt);
+    free(zc);
+    free(src);
+    free(zt);
+    free(L);
+    free(R);
+    free(warped);
+    return rc;
+}

@@ -1,0 +1,56 @@
+"""Planted mistakes in the oracle must fail its pins (no GPU).
+
+Each mutant is a copy of ``oracle/yoro_oracle.c`` with one plausible mistake (a
+dropped term, a wrong sign, index or order), built into a temporary library and
+loaded by a fresh pytest run of ``test_oracle_pins.py``.  That run must fail: if it
+passed, the pins would not tie the oracle to the paper at that point.
+"""
+import os
+import subprocess
+import sys
+
+import pytest
+
+import oracle
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "yoro_oracle.c")
+
+MUTANTS = {
+    "pixel_centre_dropped": ("float t = ((float)x + 0.5f) - disp;", "float t = (float)x - disp;"),
+    "disparity_sign": ("float t = ((float)x + 0.5f) - disp;", "float t = ((float)x + 0.5f) + disp;"),
+    "round_not_floor": ("float f = floorf(t);", "float f = rintf(t);"),
+    "trunc_not_floor": ("float f = floorf(t);", "float f = truncf(t);"),
+    "no_near_clamp": ("float c = fminf(fmaxf(z, near_), far_);", "float c = fminf(z, far_);"),
+    "farther_wins": ("if (src[o] < 0 || zc[i] < zt[o]) {", "if (src[o] < 0 || zc[i] > zt[o]) {"),
+    "last_writer_wins_ties": ("if (src[o] < 0 || zc[i] < zt[o]) {", "if (src[o] < 0 || zc[i] <= zt[o]) {"),
+    "t_from_occluder_edge": ("float t = (float)(R - u) / (float)wd;", "float t = (float)(u - L) / (float)wd;"),
+    "weight_constant": ("float b = (0.3f * wrem) * t;", "float b = (0.25f * wrem) * t;"),
+    "weight_half_term": ("float a = wrem * 0.5f;", "float a = wrem * 0.4f;"),
+    "no_depth_gate": ("if (zt[q] < d_occ) continue;", ""),
+    "gate_on_background_edge": ("float d_occ = (L >= 0) ? zt[(size_t)v * (size_t)w + (size_t)L] : 0.0f;",
+                                "float d_occ = zt[(size_t)v * (size_t)w + (size_t)R];"),
+    "nearest_column_first": ("for (int j = jhi; j >= R; --j) {", "for (int j = R; j <= jhi; ++j) {"),
+    "kernel_one_column_short": ("int jhi = R + wd;", "int jhi = R + wd - 1;"),
+    "single_row_kernel": ("for (int vv = v - 1; vv <= v + 1; ++vv) {", "for (int vv = v; vv <= v; ++vv) {"),
+    "divide_by_wrem": ("float den = 1.0f - wrem;", "float den = wrem;"),
+    "fallback_to_occluder": ("    if (R < w)\n        memcpy(out, warped + 4 * ((size_t)v * (size_t)w + (size_t)R), 4);",
+                             "    if (L >= 0)\n        memcpy(out, warped + 4 * ((size_t)v * (size_t)w + (size_t)L), 4);"),
+    "alpha_not_filled": ("for (int c = 0; c < 4; ++c) {\n                float r", "for (int c = 0; c < 3; ++c) {\n                float r"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_catch_mutant(name, tmp_path):
+    old, new = MUTANTS[name]
+    src = open(SRC).read()
+    assert src.count(old) == 1, f"mutation site for {name} not found exactly once"
+    mut_c = tmp_path / "mutant.c"
+    mut_c.write_text(src.replace(old, new))
+    lib = tmp_path / "libmutant.so"
+    subprocess.check_call(["gcc", *oracle.CFLAGS, "-shared", "-fPIC", "-o", str(lib), str(mut_c), "-lm"])
+    env = dict(os.environ, YORO_ORACLE_LIB=str(lib))
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode != 0, f"mutant {name} passed every pin:\n{r.stdout[-2000:]}"
