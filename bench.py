@@ -1,0 +1,370 @@
+"""Benchmark: right-eye synthesis throughput at 1832x1920 on GB300.
+
+One step = the whole path (disparity, nearest-wins warp, gather, hole edges, hole
+fill) over one 1832x1920 frame through the C ABI (``yoro_synthesize``), inputs
+already resident in HBM.  Frames rotate through a pool of distinct seeded scenes
+whose inputs and outputs together exceed twice the L2 size, so every step reads
+and writes HBM.  Prints one JSON line (rank 0).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl yoro|reference]
+
+Multi-GPU: one process per GPU (torchrun); every rank synthesizes its own frames
+(independent replicas, no collective on the data path; scaling "weak"), and the
+value is the frames of all ranks over the slowest rank's time.
+
+``--impl reference`` times the CPU oracle (the definition of the method, plain C,
+one host core) on the same workload; under torchrun only rank 0 runs it.
+"""
+from __future__ import annotations
+
+import argparse
+import glob
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "2nd-eye Mpix/s and frames/s at 1832x1920 (% HBM peak); p50/p99 frame latency"
+UNIT = "Mpix/s"
+BYTES_PER_PIXEL = 13  # read 4 B depth + 4 B color, write 4 B color + 1 B mask
+KERNEL = "fused_single"
+CSRC = os.path.join(ROOT, "paper_2506_15183_gb300", "csrc")
+PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20000)
+    p.add_argument("--warmup", type=int, default=200)
+    p.add_argument("--impl", choices=["yoro", "reference"], default="yoro")
+    p.add_argument("--pool", type=int, default=0, help="frames in the rotating pool (0: auto, >= 8)")
+    p.add_argument("--cpu-seconds", type=float, default=10.0, help="bounded CPU-oracle sample")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def csrc_digest() -> str:
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(CSRC, "*"))):
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def ncu_traffic():
+    """Per-launch DRAM bytes of the timed kernel from the committed ncu summary, if it was
+    taken on the current kernel sources; else None."""
+    if not os.path.exists(PROFILE_TRAFFIC):
+        return None
+    d = json.load(open(PROFILE_TRAFFIC))
+    if d.get("csrc_digest") != csrc_digest():
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=5)
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in self.rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def make_pool(cfg, n_frames, device):
+    import torch
+
+    from paper_2506_15183_gb300 import scene
+
+    pool = []
+    for i in range(n_frames):
+        c, d, _ = scene.render(cfg, 1 + i)
+        pool.append(dict(color=torch.from_numpy(c).to(device), depth=torch.from_numpy(d).to(device),
+                         out=torch.empty((cfg.h, cfg.w, 4), dtype=torch.uint8, device=device),
+                         mask=torch.empty((cfg.h, cfg.w), dtype=torch.uint8, device=device),
+                         host=(c, d)))
+    return pool
+
+
+def cpu_baseline(cfg, frames, seconds):
+    """The oracle as it stands, one host core, on pool frames until `seconds` have passed."""
+    import oracle
+
+    n = 0
+    t0 = time.perf_counter()
+    while True:
+        c, d = frames[n % len(frames)]
+        oracle.synthesize(c, d, cfg.fx, cfg.fy, cfg.cx, cfg.cy, cfg.ipd, cfg.near, cfg.far)
+        n += 1
+        dt = time.perf_counter() - t0
+        if dt >= seconds and n >= 3:
+            break
+    return {"value": round(n * cfg.w * cfg.h / dt / 1e6, 3), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{n} frames of the 1832x1920 workload (seeds 1-{min(n, len(frames))}), "
+                      f"{dt:.1f} s on one host core"}
+
+
+def run_reference(args, rank, world):
+    from paper_2506_15183_gb300 import scene
+
+    if rank != 0:
+        return
+    import oracle
+
+    oracle.build()
+    cfg = scene.quest_config()
+    frames = [scene.render(cfg, 1 + i)[:2] for i in range(4)]
+    for i in range(args.warmup):
+        c, d = frames[i % len(frames)]
+        oracle.synthesize(c, d, cfg.fx, cfg.fy, cfg.cx, cfg.cy, cfg.ipd, cfg.near, cfg.far)
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        c, d = frames[i % len(frames)]
+        oracle.synthesize(c, d, cfg.fx, cfg.fy, cfg.cx, cfg.cy, cfg.ipd, cfg.near, cfg.far)
+    dt = time.perf_counter() - t0
+    mpix = args.steps * cfg.w * cfg.h / dt / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(mpix, 3), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * dt / args.steps, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "quest 1832x1920: 200 primitives + ground plane, front depth log-uniform 0.1-100 m, "
+                               "IPD 0.063 m, 90 deg HFOV, seeds 1-4", "w": cfg.w, "h": cfg.h},
+        "frames_per_s": round(args.steps / dt, 3),
+        "cpu_baseline": {"value": round(mpix, 3), "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} frames of the 1832x1920 workload on one host core"},
+        "e2e": {"value": round(mpix, 3), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+
+    import paper_2506_15183_gb300 as yoro
+    from paper_2506_15183_gb300 import scene
+
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    device = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(device)
+    lib = yoro.load_library()
+
+    cfg = scene.quest_config()
+    npx = cfg.w * cfg.h
+    l2 = torch.cuda.get_device_properties(device).L2_cache_size
+    pool_n = args.pool or max(8, int(np.ceil(2 * l2 / (BYTES_PER_PIXEL * npx))) + 1)
+    pool = make_pool(cfg, pool_n, device)
+    hdl = yoro.yoro_create(**cfg.camera())
+    stream = torch.cuda.Stream(device)
+    s_ptr = stream.cuda_stream
+    calls = [(hdl.ptr, f["color"].data_ptr(), f["depth"].data_ptr(), f["out"].data_ptr(), f["mask"].data_ptr(),
+              s_ptr) for f in pool]
+    synth = lib.yoro_synthesize
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    # warm-up
+    for i in range(args.warmup):
+        rc = synth(*calls[i % pool_n])
+        if rc:
+            raise yoro.YoroError(rc, "yoro_synthesize")
+    stream.synchronize()
+
+    # timed region: K back-to-back frames on one stream
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize(device)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for i in range(args.steps):
+        synth(*calls[i % pool_n])
+    ev1.record(stream)
+    stream.synchronize()
+    barrier()
+    torch.cuda.synchronize(device)
+    clk = clocks.stop()
+    t_ms = ev0.elapsed_time(ev1)
+    if world > 1:
+        t = torch.tensor([t_ms], device=device)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_ms = float(t.item())
+    status = yoro.yoro_stream_status(hdl, stream)
+    if status != 0:
+        raise yoro.YoroError(status, "kernel status")
+
+    # per-frame device latency: one frame at a time, event pair around each launch
+    lat = []
+    n_lat = min(2000, max(200, args.steps // 10))
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_lat)]
+    for i, (a, b) in enumerate(evs):
+        a.record(stream)
+        synth(*calls[i % pool_n])
+        b.record(stream)
+    stream.synchronize()
+    lat = sorted(a.elapsed_time(b) * 1e3 for a, b in evs)  # us
+
+    # end-to-end through the host-buffer entry point: H2D inputs, kernel, D2H outputs per step
+    e2e = run_e2e(yoro, lib, cfg, pool, device, steps=min(args.steps, 400), warmup=10)
+
+    frames = args.steps * world
+    secs = t_ms / 1e3
+    mpix = frames * npx / secs / 1e6
+    per_launch_s = secs / args.steps
+    peak, peak_kind = measured_peaks()
+    achieved = BYTES_PER_PIXEL * npx / per_launch_s / 1e9
+    line = {
+        "metric": METRIC, "value": round(mpix, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(t_ms / args.steps, 5), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "quest 1832x1920: 200 primitives + ground plane, front depth log-uniform 0.1-100 m, "
+                               "IPD 0.063 m, 90 deg HFOV", "w": cfg.w, "h": cfg.h, "pool_frames": pool_n,
+                   "l2_flush": f"rotating pool of {pool_n} frames ({pool_n * BYTES_PER_PIXEL * npx / 1e6:.0f} MB "
+                               f"of inputs+outputs) > 2x L2 ({l2 / 1e6:.0f} MB)",
+                   "parallelism": f"replicas{world}", "entry_point": "yoro_synthesize"},
+        "frames_per_s": round(frames / secs, 1),
+        "hbm_frac_of_peak": round(achieved / peak, 4),
+        "latency_us": {"p50": round(lat[len(lat) // 2], 2), "p99": round(lat[int(0.99 * (len(lat) - 1))], 2),
+                       "what": "device time of one frame launched alone (CUDA events around one call)",
+                       "samples": len(lat)},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "traffic": ncu_traffic(),
+                     "kernel": KERNEL, "bytes_per_launch": BYTES_PER_PIXEL * npx,
+                     "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
+                     else "fallback 6.8 TB/s"},
+        "e2e": e2e,
+        "gpu_launches": args.steps,
+        "clocks": clk,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(cfg, [f["host"] for f in pool], args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    yoro.yoro_destroy(hdl)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def run_e2e(yoro, lib, cfg, pool, device, steps, warmup):
+    """Throughput through yoro_synthesize_host with pinned host buffers: each step copies
+    its inputs host->device, synthesizes, and copies the right eye and mask back.  Three
+    handles on three streams let copies of one frame overlap the kernel of another."""
+    import torch
+
+    npx = cfg.w * cfg.h
+    nslot = 3
+    hosts = []
+    for i in range(nslot):
+        c, d = pool[i % len(pool)]["host"]
+        hosts.append((torch.from_numpy(c).pin_memory(), torch.from_numpy(d).pin_memory(),
+                      torch.empty((cfg.h, cfg.w, 4), dtype=torch.uint8).pin_memory(),
+                      torch.empty((cfg.h, cfg.w), dtype=torch.uint8).pin_memory()))
+    streams = [torch.cuda.Stream(device) for _ in range(nslot)]
+    handles = [yoro.yoro_create(**cfg.camera()) for _ in range(nslot)]
+    calls = [(handles[i].ptr, *[t.data_ptr() for t in hosts[i]], streams[i].cuda_stream) for i in range(nslot)]
+    fn = lib.yoro_synthesize_host
+    for i in range(warmup):
+        fn(*calls[i % nslot])
+    torch.cuda.synchronize(device)
+    t0 = time.perf_counter()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev0.record(streams[0])
+    for s in streams[1:]:
+        s.wait_event(ev0)
+    for i in range(steps):
+        rc = fn(*calls[i % nslot])
+        if rc:
+            raise yoro.YoroError(rc, "yoro_synthesize_host")
+    ends = []
+    for s in streams:
+        e = torch.cuda.Event(enable_timing=True)
+        e.record(s)
+        ends.append(e)
+    torch.cuda.synchronize(device)
+    wall = time.perf_counter() - t0
+    t_ms = max(ev0.elapsed_time(e) for e in ends)
+    for h in handles:
+        yoro.yoro_destroy(h)
+    return {"value": round(steps * npx / (t_ms / 1e3) / 1e6, 3), "unit": UNIT,
+            "h2d_bytes_per_step": 8 * npx, "d2h_bytes_per_step": 5 * npx,
+            "steps": steps, "wall_s": round(wall, 4), "entry_point": "yoro_synthesize_host (pinned host buffers)"}
+
+
+if __name__ == "__main__":
+    main()

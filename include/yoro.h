@@ -1,0 +1,153 @@
+/*
+ * yoro.h — C ABI of the GB300 second-eye synthesis library (libyoro.so).
+ *
+ * Given the rendered LEFT eye of a stereo pair (RGBA8 color and FP32 linear
+ * view-space depth), the library produces the RIGHT eye (RGBA8) and a hole mask,
+ * following "You Only Render Once" (YORO):
+ *   1. disparity per source pixel (Sec. Reprojector, Alg. 1 with Eq. 5 in closed
+ *      form for a parallel-axis pinhole pair): zc = clamp(z, near, far),
+ *      disp = (fx * ipd) / zc, target column xt = floor(x + 0.5 - disp);
+ *   2. forward warp with the nearest source kept per target (Alg. 2; on equal
+ *      depth the lowest source column wins);
+ *   3. gather: a reached target takes its source's four bytes (Alg. 3, non-hole
+ *      branch);
+ *   4. disocclusion tracking (Sec. Reprojector, strategy (b)): nearest reached
+ *      column on each side of a hole;
+ *   5. hole fill (Sec. Patcher, Alg. 3 with the weight of Eq. 6) over rows
+ *      v-1..v+1 on the background side, foreground candidates skipped (O2).
+ * Every step runs in the library's CUDA kernels (sm_103a); all arithmetic is
+ * IEEE binary32 with no fused multiply-add, so the output is a deterministic
+ * function of the inputs.
+ *
+ * Conventions shared by every entry point:
+ *   - Images are tightly packed, row-major, row 0 at the top. color / out_color
+ *     hold h*w*4 bytes (R, G, B, A per pixel), depth holds h*w floats,
+ *     out_hole_mask holds h*w bytes (1 = the pixel was a hole before the fill,
+ *     0 = reached by a source pixel).
+ *   - Pointers named device pointers must point to memory of the device that was
+ *     current when the handle was created; color/out_color/depth need 4-byte
+ *     alignment.  16-byte aligned pointers with w % 4 == 0 take the bulk-copy fast
+ *     path; other layouts are accepted and take a slower element-wise path.
+ *   - The caller owns every image buffer.  Outputs must not overlap inputs.
+ *   - Work is enqueued on the caller's CUDA stream (a cudaStream_t passed as
+ *     void*, NULL = the legacy default stream) and returns before it finishes.
+ *     Argument errors are reported synchronously; errors raised while the kernels
+ *     run surface from yoro_stream_status() or from the caller's own stream
+ *     synchronisation.
+ *   - A handle may be used from one host thread at a time.  Calls on different
+ *     streams may overlap on the GPU except where an entry point says it uses
+ *     handle-owned scratch memory.
+ */
+#ifndef YORO_H
+#define YORO_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct yoro_ctx* yoro_handle;
+
+typedef enum {
+    YORO_OK = 0,
+    YORO_EINVAL = 1,   /* bad argument: null pointer, size, camera parameter, wrong device */
+    YORO_EALIGN = 2,   /* a pointer is not 4-byte aligned                                 */
+    YORO_ENOMEM = 3,   /* a device or pinned-host allocation failed                       */
+    YORO_ECUDA = 4,    /* a CUDA runtime call or kernel launch failed                     */
+    YORO_EDEVICE = 5,  /* a kernel reported an error in the handle's status word          */
+    YORO_ETOOBIG = 6   /* the frame exceeds a limit of the requested entry point          */
+} yoro_status;
+
+/* One frame of a batch (yoro_synthesize_batch).  All pointers are device pointers. */
+typedef struct {
+    int w, h;
+    float fx, fy, cx, cy, ipd, near_, far_;
+    const void* color;           /* h*w*4 bytes RGBA8, left eye          */
+    const float* depth;          /* h*w floats, linear view-space depth  */
+    void* out_color;             /* h*w*4 bytes RGBA8, right eye         */
+    unsigned char* out_hole_mask;/* h*w bytes                            */
+} yoro_frame;
+
+/*
+ * Create a synthesis context for w x h frames of a stereo camera.
+ *   fx, fy, cx, cy: pinhole intrinsics in pixels (shared by both eyes).  Only fx
+ *     enters the result: with parallel axes and a horizontal baseline the row is
+ *     unchanged and cx cancels (Eq. 5 in closed form).
+ *   ipd: eye separation in scene units (>= 0); the right eye sits at +ipd along x.
+ *   near_, far_: depth clamp, 0 < near_ < far_ (the camera planes of Eq. 3).  A
+ *     depth that is not a positive finite number is treated as far_.
+ * Requires w >= 0, h >= 0, w * h < 2^31, fx > 0, all parameters finite.
+ * Allocates a 16-byte device status word on the current device.
+ * Returns NULL on error; yoro_last_create_error() then tells why.
+ */
+yoro_handle yoro_create(int w, int h, float fx, float fy, float cx, float cy, float ipd,
+                        float near_, float far_);
+
+/* Status of the last yoro_create() on the calling thread (YORO_OK after a success). */
+yoro_status yoro_last_create_error(void);
+
+/* Release the handle and the device memory it owns.  NULL is accepted.  Pending work
+ * that uses handle-owned scratch must have finished (synchronise first). */
+void yoro_destroy(yoro_handle h);
+
+/*
+ * Synthesize the right eye of one frame (all five steps, one fused kernel).
+ *   color_rgba8, depth_f32: device inputs (left eye).
+ *   out_color_rgba8, out_hole_mask: device outputs (right eye).
+ *   cuda_stream: cudaStream_t or NULL.
+ * Uses no handle scratch for widths up to yoro_max_fused_width(); wider frames
+ * run the global z-buffer path of yoro_synthesize_unfused() (see there).
+ * An empty frame (w * h == 0) returns YORO_OK without launching anything.
+ */
+yoro_status yoro_synthesize(yoro_handle h, const void* color_rgba8, const float* depth_f32,
+                            void* out_color_rgba8, unsigned char* out_hole_mask, void* cuda_stream);
+
+/*
+ * Same result as yoro_synthesize(), computed by separate kernels around a global
+ * z-buffer of h*w 64-bit keys (depth bits << 32 | source column) that the handle
+ * allocates on first use and keeps.  Works for any width.  Calls that share a
+ * handle must not overlap on the GPU (they share the z-buffer).
+ */
+yoro_status yoro_synthesize_unfused(yoro_handle h, const void* color_rgba8, const float* depth_f32,
+                                    void* out_color_rgba8, unsigned char* out_hole_mask,
+                                    void* cuda_stream);
+
+/*
+ * yoro_synthesize() for HOST buffers: copies color and depth to device staging
+ * owned by the handle (allocated on first use), runs the fused kernel, and copies
+ * the right eye and mask back, all on cuda_stream.  Page-locked (pinned) host
+ * buffers give asynchronous copies; the call returns before the copies finish,
+ * so the caller synchronises the stream before reading the outputs.  Calls that
+ * share a handle must not overlap on the GPU (they share the staging).
+ */
+yoro_status yoro_synthesize_host(yoro_handle h, const void* host_color_rgba8, const float* host_depth_f32,
+                                 void* host_out_color_rgba8, unsigned char* host_out_hole_mask,
+                                 void* cuda_stream);
+
+/*
+ * Synthesize n independent frames of possibly different sizes and cameras in one
+ * persistent kernel launch (the same five steps per frame; results equal n calls of
+ * yoro_synthesize).  frames: host array of n descriptors with device pointers.
+ * Needs no handle; allocates nothing.  Returns YORO_ETOOBIG if a frame is wider than
+ * yoro_max_fused_width() or if n exceeds 4096.
+ */
+yoro_status yoro_synthesize_batch(int n, const yoro_frame* frames, void* cuda_stream);
+
+/*
+ * Synchronise cuda_stream, then read and clear the handle's device status word.
+ * Returns YORO_EDEVICE if a kernel of this handle reported an error (a bounded
+ * wait for a bulk copy ran out), YORO_ECUDA if the stream reports a CUDA error,
+ * else YORO_OK.
+ */
+yoro_status yoro_stream_status(yoro_handle h, void* cuda_stream);
+
+/* Widest frame the fused single-kernel path handles on the current device. */
+int yoro_max_fused_width(void);
+
+/* Static English description of a status code. */
+const char* yoro_status_string(yoro_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* YORO_H */

@@ -1,0 +1,213 @@
+"""GB300 second-eye synthesis (YORO): Python binding of ``libyoro.so``.
+
+The functions below carry the names of the C ABI in ``include/yoro.h`` and only
+marshal arguments (tensor checks, pointers, streams); every step of the path runs
+in the library's CUDA kernels.  PyTorch supplies device memory and streams.  The
+library is loaded from ``paper_2506_15183_gb300/_lib/libyoro.so``; if it has not
+been built, every call raises ``RuntimeError`` (there is no CPU fallback).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+__all__ = [
+    "YoroError", "Synthesizer", "load_library", "yoro_create", "yoro_destroy", "yoro_synthesize",
+    "yoro_synthesize_unfused", "yoro_synthesize_host", "yoro_synthesize_batch", "yoro_stream_status",
+    "yoro_max_fused_width", "yoro_status_string", "yoro_last_create_error", "STATUS",
+]
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "libyoro.so")
+_lib = None
+
+STATUS = {0: "YORO_OK", 1: "YORO_EINVAL", 2: "YORO_EALIGN", 3: "YORO_ENOMEM", 4: "YORO_ECUDA",
+          5: "YORO_EDEVICE", 6: "YORO_ETOOBIG"}
+
+
+class YoroError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {STATUS.get(code, code)} ({_status_string(code)})")
+
+
+class _Frame(ctypes.Structure):
+    _fields_ = [("w", ctypes.c_int), ("h", ctypes.c_int),
+                ("fx", ctypes.c_float), ("fy", ctypes.c_float), ("cx", ctypes.c_float),
+                ("cy", ctypes.c_float), ("ipd", ctypes.c_float), ("near_", ctypes.c_float),
+                ("far_", ctypes.c_float),
+                ("color", ctypes.c_void_p), ("depth", ctypes.c_void_p),
+                ("out_color", ctypes.c_void_p), ("out_hole_mask", ctypes.c_void_p)]
+
+
+def load_library(path: str | None = None) -> ctypes.CDLL:
+    """Load libyoro.so (built by ``__graft_entry__.build()``); raise if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or _LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError(f"libyoro.so not built ({path}); run __graft_entry__.build() first")
+    lib = ctypes.CDLL(path)
+    P, I, F = ctypes.c_void_p, ctypes.c_int, ctypes.c_float
+    lib.yoro_create.argtypes = [I, I, F, F, F, F, F, F, F]
+    lib.yoro_create.restype = P
+    lib.yoro_last_create_error.argtypes = []
+    lib.yoro_last_create_error.restype = I
+    lib.yoro_destroy.argtypes = [P]
+    lib.yoro_destroy.restype = None
+    for name in ("yoro_synthesize", "yoro_synthesize_unfused", "yoro_synthesize_host"):
+        fn = getattr(lib, name)
+        fn.argtypes = [P, P, P, P, P, P]
+        fn.restype = I
+    lib.yoro_synthesize_batch.argtypes = [I, ctypes.POINTER(_Frame), P]
+    lib.yoro_synthesize_batch.restype = I
+    lib.yoro_stream_status.argtypes = [P, P]
+    lib.yoro_stream_status.restype = I
+    lib.yoro_max_fused_width.argtypes = []
+    lib.yoro_max_fused_width.restype = I
+    lib.yoro_status_string.argtypes = [I]
+    lib.yoro_status_string.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def _status_string(code: int) -> str:
+    try:
+        return load_library().yoro_status_string(code).decode()
+    except Exception:  # noqa: BLE001 - message only
+        return "?"
+
+
+def _check(code: int, where: str) -> None:
+    if code != 0:
+        raise YoroError(code, where)
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, torch.cuda.Stream):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def _dev_ptr(t: torch.Tensor, dtype, shape, name: str) -> int:
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch tensor")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype or tuple(t.shape) != tuple(shape) or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous {dtype} tensor of shape {tuple(shape)}, "
+                         f"got {t.dtype} {tuple(t.shape)}")
+    return t.data_ptr()
+
+
+def _host_ptr(t: torch.Tensor, dtype, shape, name: str) -> int:
+    if t.is_cuda:
+        raise ValueError(f"{name} must be a host tensor")
+    if t.dtype != dtype or tuple(t.shape) != tuple(shape) or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous {dtype} tensor of shape {tuple(shape)}")
+    return t.data_ptr()
+
+
+class _Handle:
+    """A yoro_handle plus the frame size it was created for."""
+
+    def __init__(self, ptr: int, w: int, h: int):
+        self.ptr, self.w, self.h = ptr, w, h
+
+
+def yoro_last_create_error() -> int:
+    return load_library().yoro_last_create_error()
+
+
+def yoro_create(w, h, fx, fy, cx, cy, ipd, near, far) -> _Handle:
+    lib = load_library()
+    p = lib.yoro_create(int(w), int(h), fx, fy, cx, cy, ipd, near, far)
+    if not p:
+        raise YoroError(lib.yoro_last_create_error(), "yoro_create")
+    return _Handle(p, int(w), int(h))
+
+
+def yoro_destroy(h: _Handle) -> None:
+    if h is not None and h.ptr:
+        load_library().yoro_destroy(h.ptr)
+        h.ptr = None
+
+
+def _frame_ptrs(h: _Handle, color, depth, out_color, out_mask, ptr):
+    return (ptr(color, torch.uint8, (h.h, h.w, 4), "color"), ptr(depth, torch.float32, (h.h, h.w), "depth"),
+            ptr(out_color, torch.uint8, (h.h, h.w, 4), "out_color"),
+            ptr(out_mask, torch.uint8, (h.h, h.w), "out_hole_mask"))
+
+
+def yoro_synthesize(h: _Handle, color, depth, out_color, out_mask, stream=None) -> None:
+    """Right eye of one frame into out_color/out_mask (device tensors), on `stream`."""
+    p = _frame_ptrs(h, color, depth, out_color, out_mask, _dev_ptr)
+    _check(load_library().yoro_synthesize(h.ptr, *p, _stream(stream)), "yoro_synthesize")
+
+
+def yoro_synthesize_unfused(h: _Handle, color, depth, out_color, out_mask, stream=None) -> None:
+    p = _frame_ptrs(h, color, depth, out_color, out_mask, _dev_ptr)
+    _check(load_library().yoro_synthesize_unfused(h.ptr, *p, _stream(stream)), "yoro_synthesize_unfused")
+
+
+def yoro_synthesize_host(h: _Handle, color, depth, out_color, out_mask, stream=None) -> None:
+    """Host tensors in and out (pinned for asynchronous copies); synchronise before reading."""
+    p = _frame_ptrs(h, color, depth, out_color, out_mask, _host_ptr)
+    _check(load_library().yoro_synthesize_host(h.ptr, *p, _stream(stream)), "yoro_synthesize_host")
+
+
+def yoro_synthesize_batch(frames, stream=None) -> None:
+    """frames: sequence of dicts with keys w, h, fx, fy, cx, cy, ipd, near, far, color, depth,
+    out_color, out_mask (device tensors)."""
+    arr = (_Frame * max(len(frames), 1))()
+    for i, fr in enumerate(frames):
+        w, hh = int(fr["w"]), int(fr["h"])
+        arr[i] = _Frame(w, hh, fr["fx"], fr["fy"], fr["cx"], fr["cy"], fr["ipd"], fr["near"], fr["far"],
+                        _dev_ptr(fr["color"], torch.uint8, (hh, w, 4), "color"),
+                        _dev_ptr(fr["depth"], torch.float32, (hh, w), "depth"),
+                        _dev_ptr(fr["out_color"], torch.uint8, (hh, w, 4), "out_color"),
+                        _dev_ptr(fr["out_mask"], torch.uint8, (hh, w), "out_hole_mask"))
+    _check(load_library().yoro_synthesize_batch(len(frames), arr, _stream(stream)), "yoro_synthesize_batch")
+
+
+def yoro_stream_status(h: _Handle | None, stream=None) -> int:
+    return load_library().yoro_stream_status(h.ptr if h is not None else None, _stream(stream))
+
+
+def yoro_max_fused_width() -> int:
+    return load_library().yoro_max_fused_width()
+
+
+def yoro_status_string(code: int) -> str:
+    return _status_string(code)
+
+
+class Synthesizer:
+    """Owns a handle for one camera; ``__call__`` allocates the outputs with torch."""
+
+    def __init__(self, w, h, fx, fy, cx, cy, ipd, near=0.05, far=1000.0):
+        self.w, self.h = int(w), int(h)
+        self.handle = yoro_create(w, h, fx, fy, cx, cy, ipd, near, far)
+
+    def __call__(self, color: torch.Tensor, depth: torch.Tensor, stream=None, unfused: bool = False):
+        out = torch.empty((self.h, self.w, 4), dtype=torch.uint8, device=color.device)
+        mask = torch.empty((self.h, self.w), dtype=torch.uint8, device=color.device)
+        fn = yoro_synthesize_unfused if unfused else yoro_synthesize
+        fn(self.handle, color, depth, out, mask, stream)
+        return out, mask
+
+    def status(self, stream=None) -> int:
+        return yoro_stream_status(self.handle, stream)
+
+    def close(self) -> None:
+        yoro_destroy(self.handle)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001 - interpreter shutdown
+            pass

@@ -1,0 +1,323 @@
+// C ABI of the second-eye synthesis library: argument checks, dispatch, ownership.
+// Declarations and the contract of every entry point are in include/yoro.h.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+
+#include "yoro.h"
+#include "yoro_internal.h"
+
+using yoro::FrameArgs;
+using yoro::FusedLimits;
+
+struct yoro_ctx {
+    int w, h;
+    float fx, fy, cx, cy, ipd, near_, far_;
+    float k;
+    int device;
+    FusedLimits lim;
+    int band;
+    int* d_status;                 // 16 bytes, zeroed at creation
+    unsigned long long* d_zbuf;    // unfused path, h*w keys, allocated on first use
+    unsigned char* d_stage;        // host-buffer path, 13*h*w bytes (+ padding), on first use
+};
+
+namespace {
+
+thread_local yoro_status g_last_create = YORO_OK;
+
+// Status word of yoro_synthesize_batch (which has no handle): file-scope device memory.
+__device__ int g_batch_status[4];
+
+bool finite_all(std::initializer_list<float> v)
+{
+    for (float x : v)
+        if (!std::isfinite(x)) return false;
+    return true;
+}
+
+bool camera_ok(int w, int h, float fx, float fy, float cx, float cy, float ipd, float near_, float far_)
+{
+    if (w < 0 || h < 0) return false;
+    if ((int64_t)w * (int64_t)h >= ((int64_t)1 << 31)) return false;
+    if (!finite_all({fx, fy, cx, cy, ipd, near_, far_})) return false;
+    if (!(fx > 0.0f) || !(ipd >= 0.0f) || !(near_ > 0.0f) || !(far_ > near_)) return false;
+    return true;
+}
+
+bool aligned(const void* p, uintptr_t a) { return ((uintptr_t)p & (a - 1)) == 0; }
+
+bool overlaps(const void* a, size_t na, const void* b, size_t nb)
+{
+    const uintptr_t x = (uintptr_t)a, y = (uintptr_t)b;
+    return x < y + nb && y < x + na;
+}
+
+// Checks shared by every device-pointer entry point.  Fills `f` on success.
+yoro_status make_frame(int w, int h, float k, float near_, float far_, const void* color, const float* depth,
+                       void* out, unsigned char* mask, FrameArgs* f)
+{
+    const size_t n = (size_t)w * (size_t)h;
+    if (!color || !depth || !out || !mask) return YORO_EINVAL;
+    if (!aligned(color, 4) || !aligned(depth, 4) || !aligned(out, 4)) return YORO_EALIGN;
+    if (overlaps(out, 4 * n, color, 4 * n) || overlaps(out, 4 * n, depth, 4 * n) ||
+        overlaps(mask, n, color, 4 * n) || overlaps(mask, n, depth, 4 * n) || overlaps(mask, n, out, 4 * n))
+        return YORO_EINVAL;
+    f->color = (const uint32_t*)color;
+    f->depth = depth;
+    f->out = (uint32_t*)out;
+    f->mask = mask;
+    f->w = w;
+    f->h = h;
+    f->k = k;
+    f->near_ = near_;
+    f->far_ = far_;
+    f->band = 1;
+    f->bulk = (w % 4 == 0) && aligned(color, 16) && aligned(depth, 16) && aligned(out, 16) && aligned(mask, 4);
+    return YORO_OK;
+}
+
+yoro_status on_device(const yoro_ctx* c)
+{
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return YORO_ECUDA;
+    return dev == c->device ? YORO_OK : YORO_EINVAL;
+}
+
+yoro_status run_unfused(yoro_ctx* c, const FrameArgs& f, cudaStream_t s)
+{
+    if (!c->d_zbuf) {
+        if (cudaMalloc(&c->d_zbuf, (size_t)c->w * c->h * sizeof(unsigned long long)) != cudaSuccess) {
+            c->d_zbuf = nullptr;
+            cudaGetLastError();
+            return YORO_ENOMEM;
+        }
+    }
+    return yoro::unfused_launch(f, c->d_zbuf, s) == cudaSuccess ? YORO_OK : YORO_ECUDA;
+}
+
+yoro_status run_frame(yoro_ctx* c, FrameArgs f, cudaStream_t s)
+{
+    if (f.w > c->lim.max_width) return run_unfused(c, f, s);
+    f.band = c->band;
+    return yoro::fused_launch(f, c->lim, c->d_status, s) == cudaSuccess ? YORO_OK : YORO_ECUDA;
+}
+
+}  // namespace
+
+extern "C" {
+
+yoro_handle yoro_create(int w, int h, float fx, float fy, float cx, float cy, float ipd, float near_, float far_)
+{
+    if (!camera_ok(w, h, fx, fy, cx, cy, ipd, near_, far_)) {
+        g_last_create = YORO_EINVAL;
+        return nullptr;
+    }
+    yoro_ctx* c = new (std::nothrow) yoro_ctx();
+    if (!c) {
+        g_last_create = YORO_ENOMEM;
+        return nullptr;
+    }
+    c->w = w;
+    c->h = h;
+    c->fx = fx;
+    c->fy = fy;
+    c->cx = cx;
+    c->cy = cy;
+    c->ipd = ipd;
+    c->near_ = near_;
+    c->far_ = far_;
+    c->k = fx * ipd;  // one binary32 rounding, shared by every pixel
+    if (cudaGetDevice(&c->device) != cudaSuccess || yoro::fused_configure(c->device, &c->lim) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        g_last_create = YORO_ECUDA;
+        return nullptr;
+    }
+    c->band = yoro::fused_band_rows(c->lim, w, h);
+    if (cudaMalloc(&c->d_status, 16) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        g_last_create = YORO_ENOMEM;
+        return nullptr;
+    }
+    if (cudaMemset(c->d_status, 0, 16) != cudaSuccess) {
+        cudaFree(c->d_status);
+        delete c;
+        g_last_create = YORO_ECUDA;
+        return nullptr;
+    }
+    g_last_create = YORO_OK;
+    return c;
+}
+
+yoro_status yoro_last_create_error(void) { return g_last_create; }
+
+void yoro_destroy(yoro_handle c)
+{
+    if (!c) return;
+    if (c->d_status) cudaFree(c->d_status);
+    if (c->d_zbuf) cudaFree(c->d_zbuf);
+    if (c->d_stage) cudaFree(c->d_stage);
+    delete c;
+}
+
+yoro_status yoro_synthesize(yoro_handle c, const void* color, const float* depth, void* out_color,
+                            unsigned char* out_mask, void* stream)
+{
+    if (!c) return YORO_EINVAL;
+    if ((size_t)c->w * c->h == 0) return YORO_OK;
+    yoro_status st = on_device(c);
+    if (st != YORO_OK) return st;
+    FrameArgs f;
+    st = make_frame(c->w, c->h, c->k, c->near_, c->far_, color, depth, out_color, out_mask, &f);
+    if (st != YORO_OK) return st;
+    return run_frame(c, f, (cudaStream_t)stream);
+}
+
+yoro_status yoro_synthesize_unfused(yoro_handle c, const void* color, const float* depth, void* out_color,
+                                    unsigned char* out_mask, void* stream)
+{
+    if (!c) return YORO_EINVAL;
+    if ((size_t)c->w * c->h == 0) return YORO_OK;
+    yoro_status st = on_device(c);
+    if (st != YORO_OK) return st;
+    FrameArgs f;
+    st = make_frame(c->w, c->h, c->k, c->near_, c->far_, color, depth, out_color, out_mask, &f);
+    if (st != YORO_OK) return st;
+    return run_unfused(c, f, (cudaStream_t)stream);
+}
+
+yoro_status yoro_synthesize_host(yoro_handle c, const void* hcolor, const float* hdepth, void* hout,
+                                 unsigned char* hmask, void* stream)
+{
+    if (!c) return YORO_EINVAL;
+    const size_t n = (size_t)c->w * c->h;
+    if (n == 0) return YORO_OK;
+    if (!hcolor || !hdepth || !hout || !hmask) return YORO_EINVAL;
+    yoro_status st = on_device(c);
+    if (st != YORO_OK) return st;
+    const size_t seg = (4 * n + 255) & ~(size_t)255;
+    if (!c->d_stage) {
+        if (cudaMalloc(&c->d_stage, 3 * seg + n) != cudaSuccess) {
+            c->d_stage = nullptr;
+            cudaGetLastError();
+            return YORO_ENOMEM;
+        }
+    }
+    unsigned char* dc = c->d_stage;
+    float* dd = (float*)(c->d_stage + seg);
+    unsigned char* dout = c->d_stage + 2 * seg;
+    unsigned char* dmask = c->d_stage + 3 * seg;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cudaMemcpyAsync(dc, hcolor, 4 * n, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(dd, hdepth, 4 * n, cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return YORO_ECUDA;
+    FrameArgs f;
+    st = make_frame(c->w, c->h, c->k, c->near_, c->far_, dc, dd, dout, dmask, &f);
+    if (st != YORO_OK) return st;
+    st = run_frame(c, f, s);
+    if (st != YORO_OK) return st;
+    if (cudaMemcpyAsync(hout, dout, 4 * n, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(hmask, dmask, n, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return YORO_ECUDA;
+    return YORO_OK;
+}
+
+yoro_status yoro_synthesize_batch(int n, const yoro_frame* frames, void* stream)
+{
+    if (n < 0 || (n > 0 && !frames)) return YORO_EINVAL;
+    if (n > 4096) return YORO_ETOOBIG;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return YORO_ECUDA;
+    FusedLimits lim;
+    if (yoro::fused_configure(dev, &lim) != cudaSuccess) return YORO_ECUDA;
+    int* status = nullptr;
+    if (cudaGetSymbolAddress((void**)&status, g_batch_status) != cudaSuccess) return YORO_ECUDA;
+    // Validate everything before launching anything.
+    for (int i = 0; i < n; ++i) {
+        const yoro_frame& fr = frames[i];
+        if (!camera_ok(fr.w, fr.h, fr.fx, fr.fy, fr.cx, fr.cy, fr.ipd, fr.near_, fr.far_)) return YORO_EINVAL;
+        if (fr.w > lim.max_width) return YORO_ETOOBIG;
+        if ((size_t)fr.w * fr.h == 0) continue;
+        FrameArgs f;
+        yoro_status st = make_frame(fr.w, fr.h, fr.fx * fr.ipd, fr.near_, fr.far_, fr.color, fr.depth,
+                                    fr.out_color, fr.out_hole_mask, &f);
+        if (st != YORO_OK) return st;
+    }
+    yoro::BatchArgs* a = new (std::nothrow) yoro::BatchArgs;
+    if (!a) return YORO_ENOMEM;
+    yoro_status result = YORO_OK;
+    int i = 0;
+    while (i < n && result == YORO_OK) {
+        a->n = 0;
+        a->total_items = 0;
+        int wmax = 0;
+        for (; i < n && a->n < yoro::kMaxBatch; ++i) {
+            const yoro_frame& fr = frames[i];
+            if ((size_t)fr.w * fr.h == 0) continue;
+            FrameArgs f;
+            make_frame(fr.w, fr.h, fr.fx * fr.ipd, fr.near_, fr.far_, fr.color, fr.depth, fr.out_color,
+                       fr.out_hole_mask, &f);
+            f.band = 32;
+            a->item_start[a->n] = a->total_items;
+            a->f[a->n++] = f;
+            a->total_items += (f.h + f.band - 1) / f.band;
+            if (f.w > wmax) wmax = f.w;
+        }
+        a->item_start[a->n] = a->total_items;
+        if (a->n > 0 && yoro::fused_launch_batch(*a, wmax, lim, status, (cudaStream_t)stream) != cudaSuccess)
+            result = YORO_ECUDA;
+    }
+    delete a;
+    return result;
+}
+
+yoro_status yoro_stream_status(yoro_handle c, void* stream)
+{
+    if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) {
+        cudaGetLastError();
+        return YORO_ECUDA;
+    }
+    int* word = nullptr;
+    if (c) {
+        word = c->d_status;
+    } else if (cudaGetSymbolAddress((void**)&word, g_batch_status) != cudaSuccess) {
+        return YORO_ECUDA;
+    }
+    int v = 0;
+    if (cudaMemcpy(&v, word, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return YORO_ECUDA;
+    if (v != 0) {
+        const int zero = 0;
+        cudaMemcpy(word, &zero, sizeof(int), cudaMemcpyHostToDevice);
+        return YORO_EDEVICE;
+    }
+    return YORO_OK;
+}
+
+int yoro_max_fused_width(void)
+{
+    int dev = 0;
+    FusedLimits lim;
+    if (cudaGetDevice(&dev) != cudaSuccess || yoro::fused_configure(dev, &lim) != cudaSuccess) return 0;
+    return lim.max_width;
+}
+
+const char* yoro_status_string(yoro_status s)
+{
+    switch (s) {
+        case YORO_OK: return "ok";
+        case YORO_EINVAL: return "invalid argument";
+        case YORO_EALIGN: return "pointer not 4-byte aligned";
+        case YORO_ENOMEM: return "allocation failed";
+        case YORO_ECUDA: return "CUDA error";
+        case YORO_EDEVICE: return "kernel reported an error";
+        case YORO_ETOOBIG: return "frame exceeds a limit of this entry point";
+    }
+    return "unknown status";
+}
+
+}  // extern "C"

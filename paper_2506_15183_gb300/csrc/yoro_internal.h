@@ -1,0 +1,54 @@
+// Host/device interface between the C ABI (api.cu) and the kernel launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+namespace yoro {
+
+// One frame as the kernels see it.  color/out are RGBA8 pixels read as uint32.
+struct FrameArgs {
+    const uint32_t* color;
+    const float* depth;
+    uint32_t* out;
+    uint8_t* mask;
+    int w, h;
+    float k;      // fx * ipd, rounded once to binary32 on the host
+    float near_, far_;
+    int band;     // rows per CTA work item
+    int bulk;     // 1: rows are 16-byte aligned (w % 4 == 0), bulk copies + vector stores
+};
+
+// Up to kMaxBatch frames travel in the kernel's parameter space (< 32 KB).
+constexpr int kMaxBatch = 256;
+
+struct BatchArgs {
+    int n;
+    int total_items;
+    int item_start[kMaxBatch + 1];  // prefix sum of bands per frame
+    FrameArgs f[kMaxBatch];
+};
+
+struct FusedLimits {
+    int sms;
+    int smem_per_block;
+    int smem_per_sm;
+    int max_width;  // widest frame whose rows fit the fused kernel's shared memory
+};
+
+// fused.cu
+size_t fused_smem_bytes(int wcap);
+int fused_wcap(int w);
+int fused_threads();
+cudaError_t fused_configure(int device, FusedLimits* lim);
+int fused_band_rows(const FusedLimits& lim, int w, int h);
+cudaError_t fused_launch(const FrameArgs& f, const FusedLimits& lim, int* status, cudaStream_t stream);
+cudaError_t fused_launch_batch(const BatchArgs& a, int wmax, const FusedLimits& lim, int* status,
+                               cudaStream_t stream);
+
+// unfused.cu: separate kernels around a global z-buffer of h*w keys.
+cudaError_t unfused_launch(const FrameArgs& f, unsigned long long* zbuf, cudaStream_t stream);
+
+}  // namespace yoro

@@ -1,0 +1,81 @@
+"""The C ABI library: builds, loads without a GPU, exports every declared entry point,
+and rejects bad arguments before touching the device (no GPU needed)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER_DIR = os.path.join(ROOT, "include")
+
+
+def _declared():
+    names = []
+    for fn in sorted(os.listdir(HEADER_DIR)):
+        if not fn.endswith(".h"):
+            continue
+        src = open(os.path.join(HEADER_DIR, fn)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names += re.findall(r"^[A-Za-z_][\w \*]*?\b(yoro_\w+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2506_15183_gb300 import _build
+    import paper_2506_15183_gb300 as yoro
+
+    _build.build_cuda()
+    return yoro.load_library()
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for required in ("yoro_create", "yoro_destroy", "yoro_synthesize", "yoro_synthesize_batch",
+                     "yoro_stream_status", "yoro_last_create_error"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    from paper_2506_15183_gb300 import _build
+
+    out = subprocess.run(["nm", "-D", "--defined-only", _build.LIB], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\b(yoro_\w+)\b", out))
+    for name in _declared():
+        assert name in exported, name
+        assert getattr(lib, name) is not None
+
+
+def test_library_is_built_for_sm_103a(lib):
+    from paper_2506_15183_gb300 import _build
+
+    assert "arch=compute_103a,code=sm_103a" in _build.ARCH
+    _build.build_cuda(force=True)
+    log = open(os.path.join(_build.BUILD, "ptxas.log")).read()
+    assert "for 'sm_103a'" in log and "fused_single" in log
+
+
+def test_create_rejects_bad_camera_without_touching_the_device(lib):
+    import paper_2506_15183_gb300 as yoro
+
+    bad = [(-1, 4, 1, 1, 0, 0, 0.06, 0.05, 1000), (4, 4, 0, 1, 0, 0, 0.06, 0.05, 1000),
+           (4, 4, 1, 1, 0, 0, -0.1, 0.05, 1000), (4, 4, 1, 1, 0, 0, 0.06, 0.0, 1000),
+           (4, 4, 1, 1, 0, 0, 0.06, 2.0, 1.0), (4, 4, float("nan"), 1, 0, 0, 0.06, 0.05, 1000),
+           (65536, 65536, 1, 1, 0, 0, 0.06, 0.05, 1000)]
+    for args in bad:
+        assert lib.yoro_create(*args) is None
+        assert lib.yoro_last_create_error() == 1
+        with pytest.raises(yoro.YoroError):
+            yoro.yoro_create(*args)
+
+
+def test_null_handle_and_strings(lib):
+    assert lib.yoro_synthesize(None, None, None, None, None, None) == 1
+    assert lib.yoro_synthesize_unfused(None, None, None, None, None, None) == 1
+    assert lib.yoro_synthesize_host(None, None, None, None, None, None) == 1
+    assert lib.yoro_synthesize_batch(-1, None, None) == 1
+    lib.yoro_destroy(None)
+    for code in range(7):
+        assert lib.yoro_status_string(code)
