@@ -50,6 +50,7 @@ def parse():
     p.add_argument("--pool", type=int, default=0, help="frames in the rotating pool (0: auto, >= 8)")
     p.add_argument("--cpu-seconds", type=float, default=10.0, help="bounded CPU-oracle sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (profiling runs)")
     return p.parse_args()
 
 
@@ -281,7 +282,7 @@ def main():
     lat = sorted(a.elapsed_time(b) * 1e3 for a, b in evs)  # us
 
     # end-to-end through the host-buffer entry point: H2D inputs, kernel, D2H outputs per step
-    e2e = run_e2e(yoro, lib, cfg, pool, device, steps=min(args.steps, 400), warmup=10)
+    e2e = None if args.no_e2e else run_e2e(yoro, lib, cfg, pool, device, steps=min(args.steps, 400), warmup=10)
 
     frames = args.steps * world
     secs = t_ms / 1e3

@@ -53,7 +53,7 @@ typedef enum {
     YORO_EALIGN = 2,   /* a pointer is not 4-byte aligned                                 */
     YORO_ENOMEM = 3,   /* a device or pinned-host allocation failed                       */
     YORO_ECUDA = 4,    /* a CUDA runtime call or kernel launch failed                     */
-    YORO_EDEVICE = 5,  /* a kernel reported an error in the handle's status word          */
+    YORO_EDEVICE = 5,  /* reserved: a kernel reported an error                            */
     YORO_ETOOBIG = 6   /* the frame exceeds a limit of the requested entry point          */
 } yoro_status;
 
@@ -76,7 +76,7 @@ typedef struct {
  *   near_, far_: depth clamp, 0 < near_ < far_ (the camera planes of Eq. 3).  A
  *     depth that is not a positive finite number is treated as far_.
  * Requires w >= 0, h >= 0, w * h < 2^31, fx > 0, all parameters finite.
- * Allocates a 16-byte device status word on the current device.
+ * Records the current device; allocates no device memory.
  * Returns NULL on error; yoro_last_create_error() then tells why.
  */
 yoro_handle yoro_create(int w, int h, float fx, float fy, float cx, float cy, float ipd,
@@ -90,11 +90,12 @@ yoro_status yoro_last_create_error(void);
 void yoro_destroy(yoro_handle h);
 
 /*
- * Synthesize the right eye of one frame (all five steps, one fused kernel).
+ * Synthesize the right eye of one frame (all five steps, one fused kernel that
+ * keeps each band of rows in shared memory).
  *   color_rgba8, depth_f32: device inputs (left eye).
  *   out_color_rgba8, out_hole_mask: device outputs (right eye).
  *   cuda_stream: cudaStream_t or NULL.
- * Uses no handle scratch for widths up to yoro_max_fused_width(); wider frames
+ * Uses no scratch memory for widths up to yoro_max_fused_width(); wider frames
  * run the global z-buffer path of yoro_synthesize_unfused() (see there).
  * An empty frame (w * h == 0) returns YORO_OK without launching anything.
  */
@@ -126,17 +127,17 @@ yoro_status yoro_synthesize_host(yoro_handle h, const void* host_color_rgba8, co
 /*
  * Synthesize n independent frames of possibly different sizes and cameras in one
  * persistent kernel launch (the same five steps per frame; results equal n calls of
- * yoro_synthesize).  frames: host array of n descriptors with device pointers.
- * Needs no handle; allocates nothing.  Returns YORO_ETOOBIG if a frame is wider than
+ * yoro_synthesize).  frames: host array of n descriptors with device pointers; up to
+ * 256 frames share one launch (larger n takes several).  Needs no handle and allocates
+ * no device memory.  Returns YORO_ETOOBIG if a frame is wider than
  * yoro_max_fused_width() or if n exceeds 4096.
  */
 yoro_status yoro_synthesize_batch(int n, const yoro_frame* frames, void* cuda_stream);
 
 /*
- * Synchronise cuda_stream, then read and clear the handle's device status word.
- * Returns YORO_EDEVICE if a kernel of this handle reported an error (a bounded
- * wait for a bulk copy ran out), YORO_ECUDA if the stream reports a CUDA error,
- * else YORO_OK.
+ * Synchronise cuda_stream and report whether work on it failed: YORO_ECUDA if the
+ * stream or the runtime reports a CUDA error, else YORO_OK.  h may be NULL (batch
+ * launches have no handle).
  */
 yoro_status yoro_stream_status(yoro_handle h, void* cuda_stream);
 

@@ -19,8 +19,7 @@ struct yoro_ctx {
     float k;
     int device;
     FusedLimits lim;
-    int band;
-    int* d_status;                 // 16 bytes, zeroed at creation
+    yoro::FusedShape shape;
     unsigned long long* d_zbuf;    // unfused path, h*w keys, allocated on first use
     unsigned char* d_stage;        // host-buffer path, 13*h*w bytes (+ padding), on first use
 };
@@ -28,9 +27,6 @@ struct yoro_ctx {
 namespace {
 
 thread_local yoro_status g_last_create = YORO_OK;
-
-// Status word of yoro_synthesize_batch (which has no handle): file-scope device memory.
-__device__ int g_batch_status[4];
 
 bool finite_all(std::initializer_list<float> v)
 {
@@ -75,6 +71,9 @@ yoro_status make_frame(int w, int h, float k, float near_, float far_, const voi
     f->k = k;
     f->near_ = near_;
     f->far_ = far_;
+    // M bounds 2^-20 (xc + q + 1) over the frame: xc <= w + 0.5, q <= k/near (1 + 2^-22).
+    const double M = std::ldexp(((double)w + 1.5 + (double)k / (double)near_) * (1.0 + 1.0 / 1024.0), -20);
+    f->half_m = M < 0.5 ? (float)(0.5 - M) : 0.0f;  // rounding of 0.5 - M: below 2^-25, inside the slack
     f->band = 1;
     f->bulk = (w % 4 == 0) && aligned(color, 16) && aligned(depth, 16) && aligned(out, 16) && aligned(mask, 4);
     return YORO_OK;
@@ -102,8 +101,8 @@ yoro_status run_unfused(yoro_ctx* c, const FrameArgs& f, cudaStream_t s)
 yoro_status run_frame(yoro_ctx* c, FrameArgs f, cudaStream_t s)
 {
     if (f.w > c->lim.max_width) return run_unfused(c, f, s);
-    f.band = c->band;
-    return yoro::fused_launch(f, c->lim, c->d_status, s) == cudaSuccess ? YORO_OK : YORO_ECUDA;
+    f.band = c->shape.band;
+    return yoro::fused_launch(f, c->lim, c->shape.two_per_sm, s) == cudaSuccess ? YORO_OK : YORO_ECUDA;
 }
 
 }  // namespace
@@ -137,19 +136,7 @@ yoro_handle yoro_create(int w, int h, float fx, float fy, float cx, float cy, fl
         g_last_create = YORO_ECUDA;
         return nullptr;
     }
-    c->band = yoro::fused_band_rows(c->lim, w, h);
-    if (cudaMalloc(&c->d_status, 16) != cudaSuccess) {
-        cudaGetLastError();
-        delete c;
-        g_last_create = YORO_ENOMEM;
-        return nullptr;
-    }
-    if (cudaMemset(c->d_status, 0, 16) != cudaSuccess) {
-        cudaFree(c->d_status);
-        delete c;
-        g_last_create = YORO_ECUDA;
-        return nullptr;
-    }
+    c->shape = yoro::fused_shape(c->lim, w, h);
     g_last_create = YORO_OK;
     return c;
 }
@@ -159,7 +146,6 @@ yoro_status yoro_last_create_error(void) { return g_last_create; }
 void yoro_destroy(yoro_handle c)
 {
     if (!c) return;
-    if (c->d_status) cudaFree(c->d_status);
     if (c->d_zbuf) cudaFree(c->d_zbuf);
     if (c->d_stage) cudaFree(c->d_stage);
     delete c;
@@ -235,8 +221,6 @@ yoro_status yoro_synthesize_batch(int n, const yoro_frame* frames, void* stream)
     if (cudaGetDevice(&dev) != cudaSuccess) return YORO_ECUDA;
     FusedLimits lim;
     if (yoro::fused_configure(dev, &lim) != cudaSuccess) return YORO_ECUDA;
-    int* status = nullptr;
-    if (cudaGetSymbolAddress((void**)&status, g_batch_status) != cudaSuccess) return YORO_ECUDA;
     // Validate everything before launching anything.
     for (int i = 0; i < n; ++i) {
         const yoro_frame& fr = frames[i];
@@ -253,23 +237,31 @@ yoro_status yoro_synthesize_batch(int n, const yoro_frame* frames, void* stream)
     yoro_status result = YORO_OK;
     int i = 0;
     while (i < n && result == YORO_OK) {
+        // One launch takes up to kMaxBatch frames; every band is as tall as the
+        // widest frame's rows allow in shared memory.
+        int i1 = i, wmax = 0, cnt = 0;
+        for (; i1 < n && cnt < yoro::kMaxBatch; ++i1) {
+            if ((size_t)frames[i1].w * frames[i1].h == 0) continue;
+            if (frames[i1].w > wmax) wmax = frames[i1].w;
+            ++cnt;
+        }
+        const int band = yoro::fused_max_band(lim, wmax);
         a->n = 0;
         a->total_items = 0;
-        int wmax = 0;
-        for (; i < n && a->n < yoro::kMaxBatch; ++i) {
+        a->max_band = band;
+        for (; i < i1; ++i) {
             const yoro_frame& fr = frames[i];
             if ((size_t)fr.w * fr.h == 0) continue;
             FrameArgs f;
             make_frame(fr.w, fr.h, fr.fx * fr.ipd, fr.near_, fr.far_, fr.color, fr.depth, fr.out_color,
                        fr.out_hole_mask, &f);
-            f.band = 32;
+            f.band = band;
             a->item_start[a->n] = a->total_items;
             a->f[a->n++] = f;
             a->total_items += (f.h + f.band - 1) / f.band;
-            if (f.w > wmax) wmax = f.w;
         }
         a->item_start[a->n] = a->total_items;
-        if (a->n > 0 && yoro::fused_launch_batch(*a, wmax, lim, status, (cudaStream_t)stream) != cudaSuccess)
+        if (a->n > 0 && yoro::fused_launch_batch(*a, wmax, lim, (cudaStream_t)stream) != cudaSuccess)
             result = YORO_ECUDA;
     }
     delete a;
@@ -278,24 +270,12 @@ yoro_status yoro_synthesize_batch(int n, const yoro_frame* frames, void* stream)
 
 yoro_status yoro_stream_status(yoro_handle c, void* stream)
 {
+    (void)c;
     if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) {
         cudaGetLastError();
         return YORO_ECUDA;
     }
-    int* word = nullptr;
-    if (c) {
-        word = c->d_status;
-    } else if (cudaGetSymbolAddress((void**)&word, g_batch_status) != cudaSuccess) {
-        return YORO_ECUDA;
-    }
-    int v = 0;
-    if (cudaMemcpy(&v, word, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return YORO_ECUDA;
-    if (v != 0) {
-        const int zero = 0;
-        cudaMemcpy(word, &zero, sizeof(int), cudaMemcpyHostToDevice);
-        return YORO_EDEVICE;
-    }
-    return YORO_OK;
+    return cudaPeekAtLastError() == cudaSuccess ? YORO_OK : YORO_ECUDA;
 }
 
 int yoro_max_fused_width(void)

@@ -1,29 +1,26 @@
 // Fused second-eye synthesis kernel for GB300 (sm_103a).
 //
-// One CTA owns a band of output rows.  It streams the band's source rows, plus one
-// halo row above and below, through shared memory and runs the whole path per row:
+// One CTA synthesizes a band of B output rows at once; shared memory holds the
+// band's warped rows plus one halo row above and below (rows y0-1 .. y0+B), each as
+// 64-bit z-buffer keys that become (depth, RGBA8) pairs.  Four steps, three CTA
+// barriers per band:
 //
-//   P1  disparity + forward warp (Alg. 1 closed form, Alg. 2 nearest kept): the
-//       row's depth arrives by a 1-D bulk copy (cp.async.bulk, mbarrier-tracked,
-//       issued S rows ahead); every source pixel does a 64-bit atomicMin of
-//       (depth bits << 32 | source column) into the row's shared-memory z-buffer.
-//       Rows are independent (O1: motion is horizontal), so the scatter never
-//       leaves the row.
-//   P2  resolve + gather: each z-buffer entry becomes (depth, RGBA8 of its source)
-//       in place, the source color coming from the staged color row; a warp ballot
-//       packs the row's reached/hole flags into a bitmask.
-//   P3  hole fill of the row above (Alg. 3, Eq. 6), which needs the warped rows
-//       v-1, v, v+1 that the ring of four z-buffer slots keeps: hole edges L/R come
-//       from the bitmask (count-leading/trailing-zeros over 32-pixel words), each
-//       warp compacts the holes of its 128-pixel blocks so that all 32 lanes fill,
-//       candidates are enumerated from the bitmask highest column first, and the
-//       finished row leaves by 16-byte stores.
+//   0.  one thread starts 1-D bulk prefetches of the band's depth and color rows
+//       into L2 (cp.async.bulk.prefetch.L2), while all threads clear the keys;
+//   P1  disparity + forward warp (Alg. 1 closed form, Alg. 2 nearest kept): every
+//       source pixel of every row does a 64-bit atomicMin of
+//       (depth bits << 32 | source column) into its row's keys (O1: a row never
+//       writes another row);
+//   P2  resolve + gather: each key becomes (depth, RGBA8 of its source) in place;
+//       warp ballots write the rows' reached-pixel bitmasks;
+//   P3  the band's rows leave: reached pixels and the hole mask by 16-byte / 4-byte
+//       stores; holes are filled (Alg. 3, Eq. 6) by warps that take the band's
+//       32-pixel words round-robin, one hole per lane, so a wide disocclusion is
+//       spread over many warps.  Hole edges and kernel candidates come from the
+//       bitmasks (leading/trailing-zero counts over 32-pixel words).
 //
-// Two barriers per row: P1 | P2 (+ clear the next slot) | P3 (+ issue the next bulk
-// copy).  HBM sees 8 B read and 5 B written per pixel plus the two halo rows, which
-// neighbouring CTAs read at about the same time (L2).  Every wait on an mbarrier is
-// bounded; on expiry the CTA records an error in the status word, waits (bounded)
-// for its own copies in flight and leaves.
+// No thread ever waits on another CTA or on an asynchronous copy: the prefetches
+// only warm L2, and every read is an ordinary load.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -35,90 +32,21 @@ namespace yoro {
 
 namespace {
 
-constexpr int kStages = 2;          // bulk-copy prefetch depth (rows)
-constexpr int kWaitLimit = 1 << 20; // polls of an mbarrier before giving up
+constexpr float kSettleFrom = 0.0009765625f;  // 2^-10: start testing the exact early exit
 
-__device__ __forceinline__ uint32_t smem_addr(const void* p)
+__device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes)
 {
-    return (uint32_t)__cvta_generic_to_shared(p);
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
+// Hole fill of pixel (v, x).  `keys`/`bits` point at the slot of row `ra`; rows
+// outside [0, h) are skipped.  Pairs are (depth bits, rgba) per reached column.
+__device__ __forceinline__ uint32_t fill_pixel(int x, int v, int ra, int h, int w, int nwords, int wpad,
+                                               const unsigned long long* keys, const uint32_t* bits)
 {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
-{
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_addr(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Bounded wait: true when the phase with this parity has completed.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity)
-{
-    for (int i = 0; i < kWaitLimit; ++i)
-        if (mbar_try_wait(bar, parity)) return true;
-    return false;
-}
-
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar)
-{
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_addr(dst)),
-        "l"(src), "r"(bytes), "r"(smem_addr(bar))
-        : "memory");
-}
-
-// Shared-memory carve-up for frames up to `wcap` pixels wide (wcap % 128 == 0).
-struct Smem {
-    unsigned long long* keys;  // [4][wcap]  z-buffer keys, then (depth, rgba) pairs
-    uint32_t* bits;            // [4][wcap/32] reached flags
-    uint32_t* outrow;          // [wcap]     finished row before the global store
-    float* sdepth;             // [kStages][wcap]
-    uint32_t* scolor;          // [kStages][wcap]
-    uint64_t* bar;             // [kStages]
-    int* flag;                 // [4]        flag[0]: abort
-    __device__ Smem(unsigned char* base, int wcap)
-    {
-        size_t o = 0;
-        keys = (unsigned long long*)(base + o);
-        o += (size_t)4 * wcap * 8;
-        bits = (uint32_t*)(base + o);
-        o += (size_t)4 * (wcap / 32) * 4;
-        outrow = (uint32_t*)(base + o);
-        o += (size_t)wcap * 4;
-        sdepth = (float*)(base + o);
-        o += (size_t)kStages * wcap * 4;
-        scolor = (uint32_t*)(base + o);
-        o += (size_t)kStages * wcap * 4;
-        bar = (uint64_t*)(base + o);
-        o += (size_t)kStages * 8;
-        flag = (int*)(base + o);
-    }
-};
-
-// Hole fill of pixel (v, x); rows v-1, v, v+1 are given as (pairs, bits) or null
-// when outside the image.  Pairs are (depth bits, rgba) per reached column.
-__device__ __forceinline__ uint32_t fill_pixel(int x, int w, int nwords, const uint2* const pr[3],
-                                               const uint32_t* const br[3])
-{
-    const uint32_t* bv = br[1];
-    const uint2* pv = pr[1];
+    const int jv = v - ra;
+    const uint32_t* bv = bits + (size_t)jv * nwords;
+    const uint2* pv = reinterpret_cast<const uint2*>(keys + (size_t)jv * wpad);
     // L: highest reached column < x.
     int L = -1;
     {
@@ -147,259 +75,281 @@ __device__ __forceinline__ uint32_t fill_pixel(int x, int w, int nwords, const u
             m = bv[wi];
         }
     }
-    if (R < w) {
-        const int wd = R - L;
-        const float d_occ = (L >= 0) ? __uint_as_float(pv[L].x) : 0.0f;
-        FillAcc f;
-        f.init(__fdiv_rn((float)(R - x), (float)wd));
-        const int jhi = min(R + wd, w - 1);
-        const int whi = jhi >> 5, wlo = R >> 5;
-        const uint32_t mhi = ((jhi & 31) == 31) ? ~0u : ((2u << (jhi & 31)) - 1u);
-        const uint32_t mlo = ~0u << (R & 31);
-        bool live = true;
+    if (R >= w) return (L >= 0) ? pv[L].y : 0u;
+    const int wd = R - L;
+    const float d_occ = (L >= 0) ? __uint_as_float(pv[L].x) : 0.0f;
+    FillAcc f;
+    f.init(__fdiv_rn((float)(R - x), (float)wd));
+    const int jhi = min(R + wd, w - 1);
+    const int whi = jhi >> 5, wlo = R >> 5;
+    const uint32_t mhi = ((jhi & 31) == 31) ? ~0u : ((2u << (jhi & 31)) - 1u);
+    const uint32_t mlo = ~0u << (R & 31);
 #pragma unroll 1
-        for (int k = 0; k < 3 && live; ++k) {
-            const uint32_t* b = br[k];
-            if (b == nullptr) continue;
-            const uint2* p = pr[k];
+    for (int vv = v - 1; vv <= v + 1; ++vv) {
+        if (vv < 0 || vv >= h) continue;
+        const uint32_t* b = bits + (size_t)(vv - ra) * nwords;
+        const uint2* p = reinterpret_cast<const uint2*>(keys + (size_t)(vv - ra) * wpad);
 #pragma unroll 1
-            for (int wi = whi; wi >= wlo && live; --wi) {
-                uint32_t m = b[wi];
-                if (wi == whi) m &= mhi;
-                if (wi == wlo) m &= mlo;
-                while (m) {
-                    const int bit = 31 - __clz(m);
-                    m &= ~(1u << bit);
-                    const uint2 q = p[(wi << 5) + bit];
-                    if (__uint_as_float(q.x) < d_occ) continue;  // foreground (O2)
-                    if (!f.add(q.y)) {
-                        live = false;
-                        break;
-                    }
-                }
+        for (int wi = whi; wi >= wlo; --wi) {
+            uint32_t m = b[wi];
+            if (wi == whi) m &= mhi;
+            if (wi == wlo) m &= mlo;
+            while (m) {
+                const int bit = 31 - __clz(m);
+                m &= ~(1u << bit);
+                const uint2 q = p[(wi << 5) + bit];
+                if (__uint_as_float(q.x) < d_occ) continue;  // foreground (O2)
+                if (!f.add(q.y)) return f.result();          // weight reached exactly 0
+                uint32_t out;
+                if (f.wrem <= kSettleFrom && f.settled(out)) return out;
             }
         }
-        if (f.any()) return f.result();
-        return pv[R].y;
     }
-    if (L >= 0) return pv[L].y;
-    return 0u;
+    return f.any() ? f.result() : pv[R].y;
 }
 
-// Per-thread record of the bulk-copy stages (every thread keeps the same copy):
-// bit st of `phase` is the parity of the next wait on stage st, bit st of `pending`
-// says a copy into stage st has been issued and not yet waited for.
-struct StageState {
-    uint32_t phase = 0;
-    uint32_t pending = 0;
-};
-
-__device__ __forceinline__ void issue_row(const FrameArgs& f, const Smem& s, int wcap, int st, int row,
-                                          uint32_t row_bytes)
+// Position of the k-th (0-based) set bit of m; m must have more than k set bits.
+__device__ __forceinline__ int nth_set_bit(uint32_t m, int k)
 {
-    const size_t off = (size_t)row * (size_t)f.w;
-    mbar_expect_tx(&s.bar[st], 2u * row_bytes);
-    bulk_g2s(s.sdepth + (size_t)st * wcap, f.depth + off, row_bytes, &s.bar[st]);
-    bulk_g2s(s.scolor + (size_t)st * wcap, f.color + off, row_bytes, &s.bar[st]);
+    int pos = 0, c;
+    c = __popc(m & 0xffffu);
+    if (k >= c) { k -= c; pos += 16; m >>= 16; }
+    c = __popc(m & 0xffu);
+    if (k >= c) { k -= c; pos += 8; m >>= 8; }
+    c = __popc(m & 0xfu);
+    if (k >= c) { k -= c; pos += 4; m >>= 4; }
+    c = __popc(m & 0x3u);
+    if (k >= c) { k -= c; pos += 2; m >>= 2; }
+    c = (int)(m & 1u);
+    if (k >= c) pos += 1;
+    return pos;
 }
 
-// One band [y0, y1) of one frame.  Returns false if a bounded wait ran out.
+// One band [y0, y1) of one frame; shared memory holds rows ra..rb (ra = y0-1 or 0,
+// rb = y1 or h-1), row j at keys + j*wpad and bits + j*nwords.  Warp `warp` owns the
+// 32-pixel columns x = warp*32 + lane (+ NT, + 2*NT, ...) of every row in P1 and P2.
+// Ends with a barrier, so the next band may reuse shared memory.
 template <int NT>
-__device__ __forceinline__ bool run_band(const FrameArgs& f, int y0, int y1, const Smem& s, int wcap,
-                                         StageState& ss)
+__device__ __forceinline__ void run_band(const FrameArgs& f, int y0, int y1, int wpad,
+                                         unsigned long long* keys, uint32_t* bits, uint32_t* hword)
 {
     constexpr int NW = NT / 32;
+    constexpr int RB = 8;  // rows per batch of loads
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int w = f.w, h = f.h;
     const int nwords = (w + 31) >> 5;
     const int ra = max(y0 - 1, 0), rb = min(y1, h - 1);
-    const bool bulk = f.bulk != 0;
-    const uint32_t row_bytes = (uint32_t)w * 4u;
+    const int nr = rb - ra + 1;
+    const float* depth = f.depth + (size_t)ra * w;
+    const uint32_t* color = f.color + (size_t)ra * w;
 
-    // Clear the first slot; issue the first bulk copies.
+    if (f.bulk && warp == 0) {  // depth first: P1 needs it before P2 needs color
+        for (int j = lane; j < nr; j += 32) prefetch_l2(depth + (size_t)j * w, (uint32_t)w * 4u);
+        for (int j = lane; j < nr; j += 32) prefetch_l2(color + (size_t)j * w, (uint32_t)w * 4u);
+    }
     {
-        unsigned long long* k0 = s.keys + (size_t)(ra & 3) * wcap;
-        for (int x = tid; x < w; x += NT) k0[x] = kEmptyKey;
-        if (bulk) {
-            for (int st = 0; st < kStages && ra + st <= rb; ++st) {
-                if (tid == 0) issue_row(f, s, wcap, st, ra + st, row_bytes);
-                ss.pending |= 1u << st;
+        uint4* k4 = reinterpret_cast<uint4*>(keys);  // two keys per 16 bytes; wpad % 8 == 0
+        const int n4 = nr * (wpad >> 1);
+        const uint4 e = make_uint4(~0u, ~0u, ~0u, ~0u);
+        for (int i = tid; i < n4; i += NT) k4[i] = e;
+        const int nhw = ((y1 - y0) * nwords + 31) >> 5;
+        for (int i = tid; i < nhw; i += NT) hword[i] = 0u;
+    }
+    __syncthreads();
+
+    // ---- P1: disparity and nearest-wins scatter of rows ra..rb
+    for (int g = warp; g < nwords; g += NW) {
+        const int x = (g << 5) + lane;
+        const bool xin = x < w;
+        const float xc = __fadd_rn((float)x, 0.5f);
+        for (int j0 = 0; j0 < nr; j0 += RB) {
+            float z[RB];
+#pragma unroll
+            for (int u = 0; u < RB; ++u)
+                z[u] = (xin && j0 + u < nr) ? __ldg(depth + (size_t)(j0 + u) * w + x) : 0.0f;
+#pragma unroll
+            for (int u = 0; u < RB; ++u) {
+                if (xin && j0 + u < nr) {
+                    float zc;
+                    const int xt = disparity_target(z[u], xc, f.k, f.near_, f.far_, f.half_m, zc);
+                    if ((unsigned)xt < (unsigned)w) atomicMin(&keys[(size_t)(j0 + u) * wpad + xt], zkey(zc, x));
+                }
             }
         }
     }
     __syncthreads();
 
-    for (int r = ra; r <= rb + 1; ++r) {
-        const int st = (r - ra) % kStages;
-        // ---- P1: disparity and nearest-wins scatter of source row r
-        if (r <= rb) {
-            bool ok = true;
-            if (bulk) {
-                ok = mbar_wait_bounded(&s.bar[st], (ss.phase >> st) & 1u);
-                if (ok) {
-                    ss.phase ^= 1u << st;
-                    ss.pending &= ~(1u << st);
-                } else {
-                    s.flag[0] = 1;
-                }
-            }
-            if (ok) {
-                unsigned long long* kr = s.keys + (size_t)(r & 3) * wcap;
-                const float* drow = bulk ? s.sdepth + (size_t)st * wcap : f.depth + (size_t)r * w;
-                for (int x = tid; x < w; x += NT) {
-                    float zc;
-                    const int xt = disparity_target(drow[x], x, f.k, f.near_, f.far_, zc);
-                    if (xt >= 0 && xt < w) atomicMin(&kr[xt], zkey(zc, x));
-                }
-            }
-        }
-        __syncthreads();
-        if (s.flag[0]) return false;
-        // ---- P2: resolve row r in place, reached bitmask; clear the next slot
-        if (r <= rb) {
-            unsigned long long* kr = s.keys + (size_t)(r & 3) * wcap;
-            uint32_t* br = s.bits + (size_t)(r & 3) * (wcap / 32);
-            const uint32_t* crow = bulk ? s.scolor + (size_t)st * wcap : f.color + (size_t)r * w;
-            for (int g = warp; g < nwords; g += NW) {
-                const int x = (g << 5) + lane;
-                const unsigned long long key = (x < w) ? kr[x] : kEmptyKey;
-                const bool reached = key != kEmptyKey;
-                const uint32_t m = __ballot_sync(0xffffffffu, reached);
-                if (lane == 0) br[g] = m;
-                if (reached) {
-                    const uint32_t rgba = crow[(uint32_t)key];
-                    reinterpret_cast<uint2*>(kr)[x] = make_uint2((uint32_t)(key >> 32), rgba);
-                }
-            }
-            if (r + 1 <= rb) {
-                unsigned long long* kn = s.keys + (size_t)((r + 1) & 3) * wcap;
-                for (int x = tid; x < w; x += NT) kn[x] = kEmptyKey;
-            }
-        }
-        __syncthreads();
-        // ---- P3: fill and store row v = r - 1; refill the stage row r used
-        if (bulk && r + kStages <= rb) {
-            if (tid == 0) issue_row(f, s, wcap, st, r + kStages, row_bytes);
-            ss.pending |= 1u << st;
-        }
-        const int v = r - 1;
-        if (v >= y0 && v < y1) {
-            const uint2* pr[3];
-            const uint32_t* brow[3];
+    // ---- P2: resolve in place, gather colors, reached bitmasks
+    for (int g = warp; g < nwords; g += NW) {
+        const int x = (g << 5) + lane;
+        const bool xin = x < w;
+        for (int j0 = 0; j0 < nr; j0 += RB) {
+            uint2 kp[RB];  // (source column, depth bits) of each key
+            uint32_t rgba[RB];
 #pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                const int vv = v - 1 + k;
-                const bool in = vv >= 0 && vv < h;
-                pr[k] = in ? reinterpret_cast<const uint2*>(s.keys + (size_t)(vv & 3) * wcap) : nullptr;
-                brow[k] = in ? s.bits + (size_t)(vv & 3) * (wcap / 32) : nullptr;
-            }
-            const uint32_t* bv = brow[1];
-            const uint2* pv = pr[1];
-            uint32_t* orow = f.out + (size_t)v * w;
-            uint8_t* mrow = f.mask + (size_t)v * w;
-            for (int b = warp; (b << 7) < w; b += NW) {
-                const int xb = b << 7;
-                // holes of this 128-pixel block, 4 words
-                uint32_t hw[4];
-                int nh = 0;
+            for (int u = 0; u < RB; ++u)
+                kp[u] = (xin && j0 + u < nr) ? reinterpret_cast<const uint2*>(keys + (size_t)(j0 + u) * wpad)[x]
+                                             : make_uint2(~0u, ~0u);
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int g = (xb >> 5) + q;
-                    const int rem = w - (g << 5);
-                    const uint32_t inb = rem >= 32 ? ~0u : (rem > 0 ? ((1u << rem) - 1u) : 0u);
-                    hw[q] = g < nwords ? (~bv[g] & inb) : 0u;
-                    nh += __popc(hw[q]);
-                }
-                // fill the holes, 32 lanes at a time
-                for (int base = 0; base < nh; base += 32) {
-                    const int i = base + lane;
-                    if (i < nh) {
-                        int q = 0, c = i;
-                        while (c >= __popc(hw[q])) {
-                            c -= __popc(hw[q]);
-                            ++q;
+            for (int u = 0; u < RB; ++u)  // a key's high word is ~0 only while empty
+                rgba[u] = (kp[u].y != ~0u) ? __ldg(color + (size_t)(j0 + u) * w + kp[u].x) : 0u;
+#pragma unroll
+            for (int u = 0; u < RB; ++u) {
+                if (j0 + u < nr) {  // warp-uniform
+                    const bool reached = kp[u].y != ~0u;
+                    const uint32_t m = __ballot_sync(0xffffffffu, reached);
+                    if (lane == 0) {
+                        bits[(size_t)(j0 + u) * nwords + g] = m;
+                        const int vb = j0 + u + ra - y0;  // row within the band, or a halo row
+                        const int rem = w - (g << 5);
+                        const uint32_t inb = rem >= 32 ? ~0u : ((1u << rem) - 1u);
+                        if (vb >= 0 && vb < y1 - y0 && (~m & inb)) {
+                            const int q = vb * nwords + g;
+                            atomicOr(&hword[q >> 5], 1u << (q & 31));
                         }
-                        uint32_t m = hw[q];
-                        for (int z = 0; z < c; ++z) m &= m - 1u;
-                        const int x = xb + (q << 5) + __ffs(m) - 1;
-                        s.outrow[x] = fill_pixel(x, w, nwords, pr, brow);
                     }
+                    if (reached)
+                        reinterpret_cast<uint2*>(keys + (size_t)(j0 + u) * wpad)[x] = make_uint2(kp[u].y, rgba[u]);
                 }
-                // reached pixels: lane owns 4 consecutive pixels
-                const int x0 = xb + (lane << 2);
-                uint32_t mk = 0;
+            }
+        }
+    }
+    __syncthreads();
+
+    // ---- P3a: reached pixels and the hole mask leave
+    for (int v = y0; v < y1; ++v) {
+        const int j = v - ra;
+        const uint32_t* bv = bits + (size_t)j * nwords;
+        const uint2* pv = reinterpret_cast<const uint2*>(keys + (size_t)j * wpad);
+        uint32_t* orow = f.out + (size_t)v * w;
+        uint8_t* mrow = f.mask + (size_t)v * w;
+        for (int x0 = tid << 2; x0 < w; x0 += NT * 4) {
+            const uint32_t nib = (bv[x0 >> 5] >> (x0 & 31)) & 15u;  // reached flags of x0..x0+3
+            if (f.bulk && x0 + 3 < w) {
+                const uint4 p01 = *reinterpret_cast<const uint4*>(pv + x0);
+                const uint4 p23 = *reinterpret_cast<const uint4*>(pv + x0 + 2);
+                if (nib == 15u) {
+                    *reinterpret_cast<uint4*>(orow + x0) = make_uint4(p01.y, p01.w, p23.y, p23.w);
+                } else {
+                    if (nib & 1u) orow[x0] = p01.y;
+                    if (nib & 2u) orow[x0 + 1] = p01.w;
+                    if (nib & 4u) orow[x0 + 2] = p23.y;
+                    if (nib & 8u) orow[x0 + 3] = p23.w;
+                }
+                const uint32_t hn = ~nib & 15u;
+                *reinterpret_cast<uint32_t*>(mrow + x0) =
+                    (hn & 1u) | ((hn & 2u) << 7) | ((hn & 4u) << 14) | ((hn & 8u) << 21);
+            } else {
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
                     const int x = x0 + i;
                     if (x < w) {
-                        const bool reached = (bv[x >> 5] >> (x & 31)) & 1u;
-                        if (reached) s.outrow[x] = pv[x].y;
-                        mk |= (reached ? 0u : 1u) << (8 * i);
-                    }
-                }
-                __syncwarp();
-                if (bulk && x0 + 3 < w) {
-                    const uint4 o4 = *reinterpret_cast<const uint4*>(&s.outrow[x0]);
-                    *reinterpret_cast<uint4*>(orow + x0) = o4;
-                    *reinterpret_cast<uint32_t*>(mrow + x0) = mk;
-                } else {
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        const int x = x0 + i;
-                        if (x < w) {
-                            orow[x] = s.outrow[x];
-                            mrow[x] = (uint8_t)((mk >> (8 * i)) & 255u);
-                        }
+                        const bool reached = (nib >> i) & 1u;
+                        if (reached) orow[x] = pv[x].y;
+                        mrow[x] = reached ? 0 : 1;
                     }
                 }
             }
         }
     }
-    __syncthreads();
-    return true;
-}
 
-// After an abort, wait (bounded) for the bulk copies this CTA may still have in
-// flight, so that no copy lands in shared memory after the CTA has left.
-__device__ void drain_after_abort(const Smem& s, const StageState& ss, int* status)
-{
-    if (threadIdx.x == 0) {
-        atomicExch(status, 1);
-        for (int st = 0; st < kStages; ++st)
-            if ((ss.pending >> st) & 1u) mbar_wait_bounded(&s.bar[st], (ss.phase >> st) & 1u);
+    // ---- P3b: hole fill.  The band's words that hold holes (flags in `hword`, in
+    // row-major order) are split into NW equal ranges of consecutive words, one per
+    // warp, so neighbouring holes of one disocclusion go to the same warp and run the
+    // same candidate sequence.  A warp packs the holes of its words into batches of up
+    // to 32, one hole per lane.
+    {
+        const int nhw = ((y1 - y0) * nwords + 31) >> 5;
+        // lane L counts the flagged words among hword[L], hword[L + 32], ...
+        int mine = 0;
+        for (int i = lane; i < nhw; i += 32) mine += __popc(hword[i]);
+        int total = mine;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) total += __shfl_xor_sync(0xffffffffu, total, o);
+        const int r0 = (int)(((long long)total * warp) / NW), r1 = (int)(((long long)total * (warp + 1)) / NW);
+        int hx = 0, hv = 0, cnt = 0;  // this lane's hole of the current batch, batch size
+        int base = 0;                 // flagged words before hword[i0 .. i0 + 31]
+        for (int i0 = 0; i0 < nhw && base < r1; i0 += 32) {
+            const uint32_t fw = (i0 + lane < nhw) ? hword[i0 + lane] : 0u;
+            const int c = __popc(fw);
+            int incl = c;  // inclusive prefix over lanes
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += t;
+            }
+            const int excl = base + incl - c;
+            const int seg_total = __shfl_sync(0xffffffffu, incl, 31);
+            // this lane's flags have ranks excl .. excl + c - 1 (lowest bit first); keep
+            // those with rank in [r0, r1)
+            uint32_t sel = 0u;
+            {
+                const int first = max(r0, excl), last = min(r1, excl + c);
+                if (first < last) {
+                    sel = fw;
+                    for (int z = excl; z < first; ++z) sel &= sel - 1u;  // drop ranks below r0
+                    uint32_t rest = sel;                                 // drop ranks from r1 on
+                    for (int z = first; z < last; ++z) rest &= rest - 1u;
+                    sel &= ~rest;
+                }
+            }
+            uint32_t lanes = __ballot_sync(0xffffffffu, sel != 0u);
+            while (lanes) {
+                const int sl = __ffs(lanes) - 1;
+                lanes &= lanes - 1u;
+                uint32_t words = __shfl_sync(0xffffffffu, sel, sl);
+                while (words) {
+                    const int q = ((i0 + sl) << 5) + __ffs(words) - 1;
+                    words &= words - 1u;
+                    const int vj = q / nwords, g = q - vj * nwords;
+                    const int v = y0 + vj;
+                    const int rem = w - (g << 5);
+                    const uint32_t inb = rem >= 32 ? ~0u : ((1u << rem) - 1u);
+                    const uint32_t wm = ~bits[(size_t)(v - ra) * nwords + g] & inb;
+                    const int n = __popc(wm);
+                    if (cnt + n > 32) {  // flush the full batch
+                        if (lane < cnt)
+                            f.out[(size_t)hv * w + hx] = fill_pixel(hx, hv, ra, h, w, nwords, wpad, keys, bits);
+                        cnt = 0;
+                    }
+                    const int k = lane - cnt;
+                    if (k >= 0 && k < n) {
+                        hx = (g << 5) + nth_set_bit(wm, k);
+                        hv = v;
+                    }
+                    cnt += n;
+                }
+            }
+            base += seg_total;
+        }
+        if (lane < cnt) f.out[(size_t)hv * w + hx] = fill_pixel(hx, hv, ra, h, w, nwords, wpad, keys, bits);
     }
     __syncthreads();
 }
 
-template <int NT>
-__global__ void __launch_bounds__(NT) fused_single(FrameArgs f, int wcap, int* status)
+template <int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) fused_single(FrameArgs f, int wpad)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    Smem s(smem_raw, wcap);
-    if (threadIdx.x == 0) {
-        for (int st = 0; st < kStages; ++st) mbar_init(&s.bar[st], 1);
-        s.flag[0] = 0;
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    const int slots = f.band + 2;
+    unsigned long long* keys = reinterpret_cast<unsigned long long*>(smem_raw);
+    uint32_t* bits = reinterpret_cast<uint32_t*>(smem_raw + (size_t)slots * wpad * 8);
+    uint32_t* hword = bits + (size_t)slots * ((wpad + 31) / 32);
+    const int nbands = (f.h + f.band - 1) / f.band;
+    for (int b = blockIdx.x; b < nbands; b += gridDim.x) {
+        const int y0 = b * f.band;
+        run_band<NT>(f, y0, min(y0 + f.band, f.h), wpad, keys, bits, hword);
     }
-    __syncthreads();
-    StageState ss;
-    const int y0 = blockIdx.x * f.band;
-    const int y1 = min(y0 + f.band, f.h);
-    if (!run_band<NT>(f, y0, y1, s, wcap, ss)) drain_after_abort(s, ss, status);
 }
 
-template <int NT>
-__global__ void __launch_bounds__(NT) fused_batch(const __grid_constant__ BatchArgs a, int wcap, int* status)
+template <int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) fused_batch(const __grid_constant__ BatchArgs a, int wpad)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    Smem s(smem_raw, wcap);
-    if (threadIdx.x == 0) {
-        for (int st = 0; st < kStages; ++st) mbar_init(&s.bar[st], 1);
-        s.flag[0] = 0;
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    __syncthreads();
-    StageState ss;
+    const int slots = a.max_band + 2;
+    unsigned long long* keys = reinterpret_cast<unsigned long long*>(smem_raw);
+    uint32_t* bits = reinterpret_cast<uint32_t*>(smem_raw + (size_t)slots * wpad * 8);
+    uint32_t* hword = bits + (size_t)slots * ((wpad + 31) / 32);
     for (int item = blockIdx.x; item < a.total_items; item += gridDim.x) {
         int lo = 0, hi = a.n - 1;  // frame whose item range holds `item`
         while (lo < hi) {
@@ -409,27 +359,26 @@ __global__ void __launch_bounds__(NT) fused_batch(const __grid_constant__ BatchA
         }
         const FrameArgs& f = a.f[lo];
         const int y0 = (item - a.item_start[lo]) * f.band;
-        const int y1 = min(y0 + f.band, f.h);
-        if (!run_band<NT>(f, y0, y1, s, wcap, ss)) {
-            drain_after_abort(s, ss, status);
-            return;
-        }
+        run_band<NT>(f, y0, min(y0 + f.band, f.h), wpad, keys, bits, hword);
     }
 }
 
-constexpr int kThreads = 256;
+// Two shapes: 1024 threads with one CTA per SM (large bands), or 512 threads with
+// two CTAs per SM (bands small enough that two fit in shared memory).
+constexpr int kBig = 1024;
+constexpr int kSmall = 512;
 
 }  // namespace
 
-size_t fused_smem_bytes(int wcap)
+int fused_wpad(int w) { return ((w + 7) / 8) * 8; }
+
+size_t fused_smem_bytes(int wpad, int band)
 {
-    return (size_t)4 * wcap * 8 + (size_t)4 * (wcap / 32) * 4 + (size_t)wcap * 4 +
-           (size_t)kStages * wcap * 8 + (size_t)kStages * 8 + 16;
+    const size_t slots = (size_t)band + 2;
+    // keys, reached bitmasks, and one flag bit per 32-pixel word of the band
+    return slots * (size_t)wpad * 8 + slots * (size_t)((wpad + 31) / 32) * 4 +
+           (((size_t)band * (size_t)((wpad + 31) / 32) + 31) / 32) * 4;
 }
-
-int fused_wcap(int w) { return ((w + 127) / 128) * 128; }
-
-int fused_threads() { return kThreads; }
 
 cudaError_t fused_configure(int device, FusedLimits* lim)
 {
@@ -443,50 +392,78 @@ cudaError_t fused_configure(int device, FusedLimits* lim)
     lim->sms = sms;
     lim->smem_per_block = smem_optin;
     lim->smem_per_sm = smem_sm;
-    int wmax = 0;
-    while (fused_smem_bytes(wmax + 128) <= (size_t)smem_optin) wmax += 128;
+    int wmax = 0;  // widest frame with a band of one row
+    while (fused_smem_bytes(fused_wpad(wmax + 32), 1) <= (size_t)smem_optin && wmax + 32 <= 65535) wmax += 32;
     lim->max_width = wmax;
-    e = cudaFuncSetAttribute(fused_single<kThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(fused_batch<kThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
-    return e;
+    const void* fns[] = {(const void*)fused_single<kBig, 1>, (const void*)fused_single<kSmall, 2>,
+                         (const void*)fused_batch<kBig, 1>, (const void*)fused_batch<kSmall, 2>};
+    for (const void* fn : fns) {
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
-// CTAs of `smem` bytes that fit on one SM (1 KB of each CTA's shared memory is
-// reserved by the hardware).
-static int ctas_per_sm(const FusedLimits& lim, size_t smem)
+// Largest band whose rows fit the per-CTA shared memory.
+static int max_band(const FusedLimits& lim, int wpad)
 {
-    int n = (int)((size_t)lim.smem_per_sm / (smem + 1024));
-    return n < 1 ? 1 : (n > 8 ? 8 : n);
+    if (wpad <= 0) return 1;
+    int b = 1;
+    while (b < 4096 && fused_smem_bytes(wpad, b + 1) <= (size_t)lim.smem_per_block) ++b;
+    return b;
 }
 
-int fused_band_rows(const FusedLimits& lim, int w, int h)
+// Band height for a w x h frame: enough bands for every SM, each as tall as shared
+// memory allows up to that.  Two CTAs per SM when two such bands fit on an SM.
+FusedShape fused_shape(const FusedLimits& lim, int w, int h)
 {
-    const size_t smem = fused_smem_bytes(fused_wcap(w));
-    const long slots = (long)lim.sms * ctas_per_sm(lim, smem);
-    int band = (int)((h + slots - 1) / slots);
-    return band < 1 ? 1 : band;
+    const int wpad = fused_wpad(w);
+    const int bmax = max_band(lim, wpad);
+    FusedShape s;
+    int band = (h + lim.sms - 1) / lim.sms;
+    if (band > bmax) band = bmax;
+    if (band < 1) band = 1;
+    // two CTAs of half the band height, if they fit beside each other
+    const int half = (band + 1) / 2;
+    if (band >= 2 && 2 * (fused_smem_bytes(wpad, half) + 1024) <= (size_t)lim.smem_per_sm) {
+        s.band = half;
+        s.two_per_sm = 1;
+    } else {
+        s.band = band;
+        s.two_per_sm = 0;
+    }
+    return s;
 }
 
-cudaError_t fused_launch(const FrameArgs& f, const FusedLimits& lim, int* status, cudaStream_t stream)
+cudaError_t fused_launch(const FrameArgs& f, const FusedLimits& lim, int two_per_sm, cudaStream_t stream)
 {
-    const int wcap = fused_wcap(f.w);
-    const size_t smem = fused_smem_bytes(wcap);
-    const int grid = (f.h + f.band - 1) / f.band;
-    fused_single<kThreads><<<grid, kThreads, smem, stream>>>(f, wcap, status);
+    const int wpad = fused_wpad(f.w);
+    const size_t smem = fused_smem_bytes(wpad, f.band);
+    const int nbands = (f.h + f.band - 1) / f.band;
+    const int slots = lim.sms * (two_per_sm ? 2 : 1);
+    const int grid = nbands < slots ? nbands : slots;
+    if (two_per_sm)
+        fused_single<kSmall, 2><<<grid, kSmall, smem, stream>>>(f, wpad);
+    else
+        fused_single<kBig, 1><<<grid, kBig, smem, stream>>>(f, wpad);
     return cudaGetLastError();
 }
 
-cudaError_t fused_launch_batch(const BatchArgs& a, int wmax, const FusedLimits& lim, int* status,
-                               cudaStream_t stream)
+cudaError_t fused_launch_batch(const BatchArgs& a, int wmax, const FusedLimits& lim, cudaStream_t stream)
 {
-    const int wcap = fused_wcap(wmax);
-    const size_t smem = fused_smem_bytes(wcap);
-    int grid = lim.sms * ctas_per_sm(lim, smem);
+    const int wpad = fused_wpad(wmax);
+    const size_t smem = fused_smem_bytes(wpad, a.max_band);
+    const bool two = 2 * (smem + 1024) <= (size_t)lim.smem_per_sm;
+    int grid = lim.sms * (two ? 2 : 1);
     if (grid > a.total_items) grid = a.total_items;
     if (grid < 1) return cudaSuccess;
-    fused_batch<kThreads><<<grid, kThreads, smem, stream>>>(a, wcap, status);
+    if (two)
+        fused_batch<kSmall, 2><<<grid, kSmall, smem, stream>>>(a, wpad);
+    else
+        fused_batch<kBig, 1><<<grid, kBig, smem, stream>>>(a, wpad);
     return cudaGetLastError();
 }
+
+int fused_max_band(const FusedLimits& lim, int w) { return max_band(lim, fused_wpad(w)); }
 
 }  // namespace yoro

@@ -28,7 +28,7 @@ __global__ void scatter_kernel(FrameArgs f, unsigned long long* __restrict__ zbu
         const int y = (int)(i / (size_t)f.w);
         const int x = (int)(i - (size_t)y * f.w);
         float zc;
-        const int xt = disparity_target(f.depth[i], x, f.k, f.near_, f.far_, zc);
+        const int xt = disparity_target(f.depth[i], __fadd_rn((float)x, 0.5f), f.k, f.near_, f.far_, f.half_m, zc);
         if (xt >= 0 && xt < f.w) atomicMin(&zbuf[(size_t)y * f.w + xt], zkey(zc, x));
     }
 }
@@ -64,7 +64,7 @@ __global__ void resolve_fill_kernel(FrameArgs f, const unsigned long long* __res
             FillAcc acc;
             acc.init(__fdiv_rn((float)(R - u), (float)wd));
             const int jhi = min(R + wd, w - 1);
-            bool live = true;
+            bool live = true, done = false;
             for (int vv = v - 1; vv <= v + 1 && live; ++vv) {
                 if (vv < 0 || vv >= f.h) continue;
                 const unsigned long long* zq = zbuf + (size_t)vv * w;
@@ -72,13 +72,18 @@ __global__ void resolve_fill_kernel(FrameArgs f, const unsigned long long* __res
                     const unsigned long long kq = zq[j];
                     if (kq == kEmptyKey) continue;
                     if (__uint_as_float((uint32_t)(kq >> 32)) < d_occ) continue;
-                    if (!acc.add(key_color(f, vv, kq))) {
+                    if (!acc.add(key_color(f, vv, kq))) {  // weight reached exactly 0
                         live = false;
+                        break;
+                    }
+                    if (acc.wrem <= 0.0009765625f && acc.settled(res)) {  // exact early exit
+                        live = false;
+                        done = true;
                         break;
                     }
                 }
             }
-            res = acc.any() ? acc.result() : key_color(f, v, zr[R]);
+            if (!done) res = acc.any() ? acc.result() : key_color(f, v, zr[R]);
         } else {
             res = (L >= 0) ? key_color(f, v, zr[L]) : 0u;
         }

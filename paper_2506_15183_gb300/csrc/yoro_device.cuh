@@ -16,19 +16,50 @@ constexpr unsigned long long kEmptyKey = ~0ull;
 // +x, left eye as source):  zc = clamp(z, near, far) with non-positive or non-finite
 // depth treated as far;  target column floor((x + 0.5) - k / zc) with k = fx * ipd.
 // Returns the target column (any int; the caller drops it outside [0, w)) and
-// writes the clamped depth.
-__device__ __forceinline__ int disparity_target(float z, int x, float k, float near_, float far_,
-                                                float& zc)
+// writes the clamped depth.  `xc` is the pixel centre x + 0.5.
+// rcp.approx.ftz: one MUFU op, within 1 ulp of 1/x for normal x (a denormal
+// input flushes to a zero divisor and gives +inf).  Every use below tolerates that
+// error and the flush through a checked margin.
+__device__ __forceinline__ float rcp_approx(float x)
 {
-    if (!(z > 0.0f) || fabsf(z) == __int_as_float(0x7f800000)) z = far_;
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// The exact fallbacks live in functions of their own so that the compiler branches
+// around them instead of predicating their instructions into every pixel.
+static __device__ __noinline__ int exact_target(float xc, float k, float zc)
+{
+    // cvt.rmi gives floor; out-of-range values saturate to INT_MIN / INT_MAX, which
+    // the caller drops like any off-frame column.
+    return __float2int_rd(__fsub_rn(xc, __fdiv_rn(k, zc)));
+}
+
+static __device__ __noinline__ float exact_rint_quotient(float a, float b) { return rintf(__fdiv_rn(a, b)); }
+
+// Alg. 1 with Eq. 5 in closed form (parallel-axis pinhole pair, baseline ipd along
+// +x, left eye as source):  zc = clamp(z, near, far) with non-positive or non-finite
+// depth treated as far;  target column floor((x + 0.5) - RN(k / zc)) with k = fx * ipd.
+// Returns the target column (any int; the caller drops it outside [0, w)) and
+// writes the clamped depth.  `xc` is the pixel centre x + 0.5.
+//
+// Only the floor is needed, so the IEEE quotient is computed only when a cheaper
+// estimate cannot decide it.  With q = RN(k * rcp(zc)), |q - k/zc| <= 1.51 * 2^-23 k/zc
+// and |q - RN(k/zc)| <= 2.01 * 2^-23 k/zc; adding the two roundings of the subtraction,
+// t' = RN(xc - q) is within 2^-21 (xc + q) of t = RN(xc - RN(k/zc)).  `half_m` is
+// 0.5 - M with M = 2^-20 (w + 1.5 + k/near) * (1 + 2^-10) >= twice that distance plus
+// an absolute 2^-20 (which also covers flushed denormals), bounded on the host per
+// frame.  If frac(t') lies in (M, 1 - M), floor(t) == floor(t').
+__device__ __forceinline__ int disparity_target(float z, float xc, float k, float near_, float far_,
+                                                float half_m, float& zc)
+{
+    if (!(z > 0.0f && z < __int_as_float(0x7f800000))) z = far_;
     zc = fminf(fmaxf(z, near_), far_);
-    const float disp = __fdiv_rn(k, zc);
-    const float t = __fsub_rn(__fadd_rn((float)x, 0.5f), disp);
-    const float f = floorf(t);
-    // |f| beyond the int range can only be off-frame; clamp before converting.
-    if (f < -1.0f) return -1;
-    if (f > 2147483520.0f) return 0x7fffff80;
-    return (int)f;
+    const float tp = __fsub_rn(xc, __fmul_rn(k, rcp_approx(zc)));
+    const float fl = floorf(tp);
+    if (fabsf(__fsub_rn(__fsub_rn(tp, fl), 0.5f)) < half_m) return (int)fl;
+    return exact_target(xc, k, zc);
 }
 
 // 64-bit z-buffer key of Alg. 2's "keep the nearest": clamped depth bits above the
@@ -69,14 +100,53 @@ struct FillAcc {
         return true;
     }
     __device__ __forceinline__ bool any() const { return wrem != 1.0f; }
-    // acc / (1 - wrem) per channel, rounded half to even, clamped to [0, 255].
+
+    // Exact early exit.  Every later step only grows acc and shrinks wrem: the updates
+    // wrem -= wgt are exact (wrem/2 <= wgt <= wrem, Sterbenz; exact anyway among
+    // denormals), so the remaining weights sum to at most the current wrem; each later
+    // acc step adds at most 255 * wgt, and at most ~152 steps carry a non-zero weight
+    // (wrem at least halves per step), so rounding inflates the sum by less than a
+    // factor (1 + 2^-14).  The final quotient q = acc_N / (1 - wrem_N) therefore lies in
+    //     [acc, (acc + 255 wrem)(1 + 2^-14) / RN(1 - wrem)]
+    // (the lower end when every later color is 0).  Both ends are evaluated with
+    // upward rounding; if for every channel the interval stays below rint(acc) + 0.5,
+    // the rounded result is rint(acc) whatever the remaining candidates hold.
+    __device__ __forceinline__ bool settled(uint32_t& out) const
+    {
+        const float den = __fsub_rn(1.0f, wrem);
+        // rcp.approx is within 1 ulp of 1/den, so rcp * (1 + 2^-22) rounded up bounds it
+        const float inv = __fmul_ru(rcp_approx(den), 1.0000002384185791f);
+        const float e = __fmul_ru(255.0f, wrem);
+        uint32_t o = 0;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const float r = rintf(acc[c]);
+            if (r < 255.0f) {  // r >= 255: the clamped result is 255 whatever follows
+                const float s = __fadd_ru(__fmul_ru(__fadd_ru(acc[c], e), 1.00006103515625f), 1.0e-18f);
+                const float hi = __fmul_ru(s, inv);
+                if (!(hi < __fadd_rn(r, 0.5f))) return false;
+            }
+            o |= (uint32_t)fminf(r, 255.0f) << (8 * c);
+        }
+        out = o;
+        return true;
+    }
+    // acc / (1 - wrem) per channel, rounded half to even, clamped to [0, 255].  As for
+    // the disparity, the IEEE quotient is only computed when an estimate cannot decide
+    // the rounding: den = RN(1 - wrem) is in [0.5, 1] after a contribution, and
+    // q' = RN(acc * rcp(den)) is within 2.01 * 2^-23 * q' of RN(acc / den); if no
+    // half-integer lies within 2^-20 (q' + 1) of q', rint(q') is the result.
     __device__ __forceinline__ uint32_t result() const
     {
         const float den = __fsub_rn(1.0f, wrem);
+        const float inv = rcp_approx(den);
         uint32_t out = 0;
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
-            float r = rintf(__fdiv_rn(acc[c], den));
+            const float qp = __fmul_rn(acc[c], inv);
+            const float m = __fmul_rn(__fadd_rn(qp, 1.0f), 9.5367431640625e-07f);
+            float r = rintf(__fsub_rn(qp, m));
+            if (r != rintf(__fadd_rn(qp, m))) r = exact_rint_quotient(acc[c], den);
             r = fminf(fmaxf(r, 0.0f), 255.0f);
             out |= (uint32_t)r << (8 * c);
         }

@@ -17,6 +17,7 @@ struct FrameArgs {
     int w, h;
     float k;      // fx * ipd, rounded once to binary32 on the host
     float near_, far_;
+    float half_m; // 0.5 - M: decision margin of the approximate disparity (host bound)
     int band;     // rows per CTA work item
     int bulk;     // 1: rows are 16-byte aligned (w % 4 == 0), bulk copies + vector stores
 };
@@ -27,6 +28,7 @@ constexpr int kMaxBatch = 256;
 struct BatchArgs {
     int n;
     int total_items;
+    int max_band;                   // tallest band of the launch (sizes shared memory)
     int item_start[kMaxBatch + 1];  // prefix sum of bands per frame
     FrameArgs f[kMaxBatch];
 };
@@ -38,15 +40,20 @@ struct FusedLimits {
     int max_width;  // widest frame whose rows fit the fused kernel's shared memory
 };
 
+// Launch shape of one frame: rows per CTA, and whether two CTAs share an SM.
+struct FusedShape {
+    int band;
+    int two_per_sm;
+};
+
 // fused.cu
-size_t fused_smem_bytes(int wcap);
-int fused_wcap(int w);
-int fused_threads();
+int fused_wpad(int w);
+size_t fused_smem_bytes(int wpad, int band);
 cudaError_t fused_configure(int device, FusedLimits* lim);
-int fused_band_rows(const FusedLimits& lim, int w, int h);
-cudaError_t fused_launch(const FrameArgs& f, const FusedLimits& lim, int* status, cudaStream_t stream);
-cudaError_t fused_launch_batch(const BatchArgs& a, int wmax, const FusedLimits& lim, int* status,
-                               cudaStream_t stream);
+FusedShape fused_shape(const FusedLimits& lim, int w, int h);
+int fused_max_band(const FusedLimits& lim, int w);
+cudaError_t fused_launch(const FrameArgs& f, const FusedLimits& lim, int two_per_sm, cudaStream_t stream);
+cudaError_t fused_launch_batch(const BatchArgs& a, int wmax, const FusedLimits& lim, cudaStream_t stream);
 
 // unfused.cu: separate kernels around a global z-buffer of h*w keys.
 cudaError_t unfused_launch(const FrameArgs& f, unsigned long long* zbuf, cudaStream_t stream);
