@@ -141,6 +141,28 @@ yoro_status yoro_synthesize_batch(int n, const yoro_frame* frames, void* cuda_st
  */
 yoro_status yoro_stream_status(yoro_handle h, void* cuda_stream);
 
+/*
+ * yoro_synthesize_unfused() without a handle and without allocating device memory, for
+ * callers that must not call cudaMalloc where they synthesize: a compositor's per-frame
+ * callback (an allocation may synchronise the device mid-frame) or a plugin whose host
+ * owns the device-memory budget.  The paper has no counterpart; this is a library
+ * service.  Same camera parameters as yoro_create() and the same device pointers and
+ * layout as yoro_synthesize(); same result.
+ * The z-buffer is one array in the library's device memory, 2^22 keys (32 MiB), held by
+ * every GPU that loads the library until the process exits: frames with w * h greater
+ * than yoro_noalloc_max_pixels() are rejected with YORO_ETOOBIG.  The first call on a
+ * device looks up that array's device address (cudaGetSymbolAddress, no allocation);
+ * make that first call before any stream capture.  Every call clears the part of the
+ * array it uses on cuda_stream, and every call on every stream shares the array, so
+ * calls that could overlap on the GPU race: serialise them (one stream, or events).
+ */
+yoro_status yoro_synthesize_noalloc(int w, int h, float fx, float fy, float cx, float cy, float ipd,
+                                    float near_, float far_, const void* color_rgba8, const float* depth_f32,
+                                    void* out_color_rgba8, unsigned char* out_hole_mask, void* cuda_stream);
+
+/* Largest w * h that yoro_synthesize_noalloc() accepts (4,194,304). */
+int yoro_noalloc_max_pixels(void);
+
 /* Widest frame the fused single-kernel path handles on the current device. */
 int yoro_max_fused_width(void);
 

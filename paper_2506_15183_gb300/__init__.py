@@ -17,6 +17,7 @@ __all__ = [
     "YoroError", "Synthesizer", "load_library", "yoro_create", "yoro_destroy", "yoro_synthesize",
     "yoro_synthesize_unfused", "yoro_synthesize_host", "yoro_synthesize_batch", "yoro_stream_status",
     "yoro_max_fused_width", "yoro_status_string", "yoro_last_create_error", "STATUS",
+    "yoro_synthesize_noalloc", "yoro_noalloc_max_pixels",
 ]
 
 _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "libyoro.so")
@@ -69,6 +70,10 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.yoro_max_fused_width.restype = I
     lib.yoro_status_string.argtypes = [I]
     lib.yoro_status_string.restype = ctypes.c_char_p
+    lib.yoro_synthesize_noalloc.argtypes = [I, I, F, F, F, F, F, F, F, P, P, P, P, P]
+    lib.yoro_synthesize_noalloc.restype = I
+    lib.yoro_noalloc_max_pixels.argtypes = []
+    lib.yoro_noalloc_max_pixels.restype = I
     _lib = lib
     return lib
 
@@ -172,6 +177,23 @@ def yoro_synthesize_batch(frames, stream=None) -> None:
                         _dev_ptr(fr["out_color"], torch.uint8, (hh, w, 4), "out_color"),
                         _dev_ptr(fr["out_mask"], torch.uint8, (hh, w), "out_hole_mask"))
     _check(load_library().yoro_synthesize_batch(len(frames), arr, _stream(stream)), "yoro_synthesize_batch")
+
+
+def yoro_synthesize_noalloc(w, h, fx, fy, cx, cy, ipd, near, far, color, depth, out_color, out_mask,
+                            stream=None) -> None:
+    """Right eye without a handle and without device allocation (for callers that must not
+    allocate where they synthesize); frames up to yoro_noalloc_max_pixels() pixels.  Calls
+    share one scratch array in the library, so they must not overlap on the GPU."""
+    w, h = int(w), int(h)
+    p = (_dev_ptr(color, torch.uint8, (h, w, 4), "color"), _dev_ptr(depth, torch.float32, (h, w), "depth"),
+         _dev_ptr(out_color, torch.uint8, (h, w, 4), "out_color"),
+         _dev_ptr(out_mask, torch.uint8, (h, w), "out_hole_mask"))
+    _check(load_library().yoro_synthesize_noalloc(w, h, fx, fy, cx, cy, ipd, near, far, *p, _stream(stream)),
+           "yoro_synthesize_noalloc")
+
+
+def yoro_noalloc_max_pixels() -> int:
+    return load_library().yoro_noalloc_max_pixels()
 
 
 def yoro_stream_status(h: _Handle | None, stream=None) -> int:
