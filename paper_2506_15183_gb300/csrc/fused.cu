@@ -39,16 +39,13 @@ __device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes)
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
-// Hole fill of pixel (v, x).  `keys`/`bits` point at the slot of row `ra`; rows
-// outside [0, h) are skipped.  Pairs are (depth bits, rgba) per reached column.
-__device__ __forceinline__ uint32_t fill_pixel(int x, int v, int ra, int h, int w, int nwords, int wpad,
-                                               const unsigned long long* keys, const uint32_t* bits)
+// Hole edges of pixel (v, x): L = highest reached column < x (or -1), R = lowest
+// reached column > x (or w), from the row's reached bitmask.
+__device__ __forceinline__ void find_edges(int x, int v, int ra, int nwords, const uint32_t* bits, int w, int& L,
+                                           int& R)
 {
-    const int jv = v - ra;
-    const uint32_t* bv = bits + (size_t)jv * nwords;
-    const uint2* pv = reinterpret_cast<const uint2*>(keys + (size_t)jv * wpad);
-    // L: highest reached column < x.
-    int L = -1;
+    const uint32_t* bv = bits + (size_t)(v - ra) * nwords;
+    L = -1;
     {
         int wi = x >> 5;
         uint32_t m = bv[wi] & ((1u << (x & 31)) - 1u);
@@ -61,8 +58,7 @@ __device__ __forceinline__ uint32_t fill_pixel(int x, int v, int ra, int h, int 
             m = bv[wi];
         }
     }
-    // R: lowest reached column > x (bits past the row end are zero).
-    int R = w;
+    R = w;  // bits past the row end are zero
     {
         int wi = x >> 5;
         uint32_t m = ((x & 31) == 31) ? 0u : (bv[wi] & (~0u << ((x & 31) + 1)));
@@ -75,7 +71,14 @@ __device__ __forceinline__ uint32_t fill_pixel(int x, int v, int ra, int h, int 
             m = bv[wi];
         }
     }
-    if (R >= w) return (L >= 0) ? pv[L].y : 0u;
+}
+
+// Hole fill of pixel (v, x) with edges L, R (R < w).  Rows of the band are addressed
+// relative to `ra`; rows outside [0, h) are skipped.  Pairs are (depth bits, rgba).
+__device__ __forceinline__ uint32_t fill_from_edges(int x, int v, int L, int R, int ra, int h, int w, int nwords,
+                                                    int wpad, const unsigned long long* keys, const uint32_t* bits)
+{
+    const uint2* pv = reinterpret_cast<const uint2*>(keys + (size_t)(v - ra) * wpad);
     const int wd = R - L;
     const float d_occ = (L >= 0) ? __uint_as_float(pv[L].x) : 0.0f;
     FillAcc f;
@@ -108,6 +111,53 @@ __device__ __forceinline__ uint32_t fill_pixel(int x, int v, int ra, int h, int 
     return f.any() ? f.result() : pv[R].y;
 }
 
+// Fill of a batch of holes, one per lane below `cnt` (none on the image border).
+__device__ __forceinline__ uint32_t fill_batch(int cnt, int x, int v, int ra, int h, int w, int nwords, int wpad,
+                                               const unsigned long long* keys, const uint32_t* bits)
+{
+    uint32_t res = 0u;
+    if ((int)(threadIdx.x & 31) < cnt) {
+        int L, R;
+        find_edges(x, v, ra, nwords, bits, w, L, R);
+        res = fill_from_edges(x, v, L, R, ra, h, w, nwords, wpad, keys, bits);
+    }
+    return res;
+}
+
+// Hole fill of a one-pixel crack (v, x): reached pixels at x-1 and x+1, so L = x-1,
+// R = x+1, w = 2 and t = 1/2.  The kernel is rows v-1, v, v+1 times columns
+// min(x+3, W-1) .. x+1; all nine slots are visited in the same order as fill_from_edges,
+// without early exits.  A slot that does not contribute (outside the image, a hole, or
+// nearer than the occluder) is given weight 0, which leaves acc and wrem unchanged
+// exactly, so the result equals the general loop's.
+__device__ __forceinline__ uint32_t fill_crack(int x, int v, int ra, int h, int w, int nwords, int wpad,
+                                               const unsigned long long* keys, const uint32_t* bits)
+{
+    const uint2* pv = reinterpret_cast<const uint2*>(keys + (size_t)(v - ra) * wpad);
+    const float d_occ = __uint_as_float(pv[x - 1].x);
+    FillAcc f;
+    f.init(0.5f);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const int vv = v - 1 + k;
+        const bool row_in = vv >= 0 && vv < h;
+        const int j = row_in ? vv - ra : v - ra;  // a valid row to read when vv is outside
+        const uint32_t* b = bits + (size_t)j * nwords;
+        const uint2* p = reinterpret_cast<const uint2*>(keys + (size_t)j * wpad);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const int col = x + 3 - c;
+            const bool col_in = col < w;
+            const int cc = col_in ? col : x + 1;
+            const bool reached = (b[cc >> 5] >> (cc & 31)) & 1u;
+            const uint2 q = p[cc];
+            const bool contributes = row_in && col_in && reached && !(__uint_as_float(q.x) < d_occ);
+            f.add_if(contributes, q.y);
+        }
+    }
+    return f.any() ? f.result() : pv[x + 1].y;
+}
+
 // Position of the k-th (0-based) set bit of m; m must have more than k set bits.
 __device__ __forceinline__ int nth_set_bit(uint32_t m, int k)
 {
@@ -131,7 +181,7 @@ __device__ __forceinline__ int nth_set_bit(uint32_t m, int k)
 // Ends with a barrier, so the next band may reuse shared memory.
 template <int NT>
 __device__ __forceinline__ void run_band(const FrameArgs& f, int y0, int y1, int wpad,
-                                         unsigned long long* keys, uint32_t* bits, uint32_t* hword)
+                                         unsigned long long* keys, uint32_t* bits, int* ctr, int* lastr)
 {
     constexpr int NW = NT / 32;
     constexpr int RB = 8;  // rows per batch of loads
@@ -152,8 +202,7 @@ __device__ __forceinline__ void run_band(const FrameArgs& f, int y0, int y1, int
         const int n4 = nr * (wpad >> 1);
         const uint4 e = make_uint4(~0u, ~0u, ~0u, ~0u);
         for (int i = tid; i < n4; i += NT) k4[i] = e;
-        const int nhw = ((y1 - y0) * nwords + 31) >> 5;
-        for (int i = tid; i < nhw; i += NT) hword[i] = 0u;
+        if (tid == 0) *ctr = 0;
     }
     __syncthreads();
 
@@ -198,16 +247,7 @@ __device__ __forceinline__ void run_band(const FrameArgs& f, int y0, int y1, int
                 if (j0 + u < nr) {  // warp-uniform
                     const bool reached = kp[u].y != ~0u;
                     const uint32_t m = __ballot_sync(0xffffffffu, reached);
-                    if (lane == 0) {
-                        bits[(size_t)(j0 + u) * nwords + g] = m;
-                        const int vb = j0 + u + ra - y0;  // row within the band, or a halo row
-                        const int rem = w - (g << 5);
-                        const uint32_t inb = rem >= 32 ? ~0u : ((1u << rem) - 1u);
-                        if (vb >= 0 && vb < y1 - y0 && (~m & inb)) {
-                            const int q = vb * nwords + g;
-                            atomicOr(&hword[q >> 5], 1u << (q & 31));
-                        }
-                    }
+                    if (lane == 0) bits[(size_t)(j0 + u) * nwords + g] = m;
                     if (reached)
                         reinterpret_cast<uint2*>(keys + (size_t)(j0 + u) * wpad)[x] = make_uint2(kp[u].y, rgba[u]);
                 }
@@ -216,11 +256,27 @@ __device__ __forceinline__ void run_band(const FrameArgs& f, int y0, int y1, int
     }
     __syncthreads();
 
-    // ---- P3a: reached pixels and the hole mask leave
+    // Last reached column of every band row: holes right of it have no background edge
+    // (R = W) and take the fallback, the color of that last reached pixel (zero if the row
+    // has none).  They leave with the reached pixels; the fill below skips them.
+    for (int vj = warp; vj < y1 - y0; vj += NW) {
+        const uint32_t* bv = bits + (size_t)(vj + y0 - ra) * nwords;
+        int last = -1;
+        for (int g = lane; g < nwords; g += 32)
+            if (bv[g]) last = (g << 5) + 31 - __clz(bv[g]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) last = max(last, __shfl_xor_sync(0xffffffffu, last, o));
+        if (lane == 0) lastr[vj] = last;
+    }
+    __syncthreads();
+
+    // ---- P3a: reached pixels, border holes and the hole mask leave
     for (int v = y0; v < y1; ++v) {
         const int j = v - ra;
         const uint32_t* bv = bits + (size_t)j * nwords;
         const uint2* pv = reinterpret_cast<const uint2*>(keys + (size_t)j * wpad);
+        const int last = lastr[v - y0];
+        const uint32_t border = last >= 0 ? pv[last].y : 0u;
         uint32_t* orow = f.out + (size_t)v * w;
         uint8_t* mrow = f.mask + (size_t)v * w;
         for (int x0 = tid << 2; x0 < w; x0 += NT * 4) {
@@ -228,13 +284,21 @@ __device__ __forceinline__ void run_band(const FrameArgs& f, int y0, int y1, int
             if (f.bulk && x0 + 3 < w) {
                 const uint4 p01 = *reinterpret_cast<const uint4*>(pv + x0);
                 const uint4 p23 = *reinterpret_cast<const uint4*>(pv + x0 + 2);
-                if (nib == 15u) {
-                    *reinterpret_cast<uint4*>(orow + x0) = make_uint4(p01.y, p01.w, p23.y, p23.w);
+                uint4 o = make_uint4(p01.y, p01.w, p23.y, p23.w);
+                if (x0 + 0 > last) o.x = border;
+                if (x0 + 1 > last) o.y = border;
+                if (x0 + 2 > last) o.z = border;
+                if (x0 + 3 > last) o.w = border;
+                // bytes of interior holes are left to the fill
+                const uint32_t wr = nib | (x0 + 0 > last ? 1u : 0u) | (x0 + 1 > last ? 2u : 0u) |
+                                    (x0 + 2 > last ? 4u : 0u) | (x0 + 3 > last ? 8u : 0u);
+                if (wr == 15u) {
+                    *reinterpret_cast<uint4*>(orow + x0) = o;
                 } else {
-                    if (nib & 1u) orow[x0] = p01.y;
-                    if (nib & 2u) orow[x0 + 1] = p01.w;
-                    if (nib & 4u) orow[x0 + 2] = p23.y;
-                    if (nib & 8u) orow[x0 + 3] = p23.w;
+                    if (wr & 1u) orow[x0] = o.x;
+                    if (wr & 2u) orow[x0 + 1] = o.y;
+                    if (wr & 4u) orow[x0 + 2] = o.z;
+                    if (wr & 8u) orow[x0 + 3] = o.w;
                 }
                 const uint32_t hn = ~nib & 15u;
                 *reinterpret_cast<uint32_t*>(mrow + x0) =
@@ -246,6 +310,7 @@ __device__ __forceinline__ void run_band(const FrameArgs& f, int y0, int y1, int
                     if (x < w) {
                         const bool reached = (nib >> i) & 1u;
                         if (reached) orow[x] = pv[x].y;
+                        else if (x > last) orow[x] = border;
                         mrow[x] = reached ? 0 : 1;
                     }
                 }
@@ -253,76 +318,79 @@ __device__ __forceinline__ void run_band(const FrameArgs& f, int y0, int y1, int
         }
     }
 
-    // ---- P3b: hole fill.  The band's words that hold holes (flags in `hword`, in
-    // row-major order) are split into NW equal ranges of consecutive words, one per
-    // warp, so neighbouring holes of one disocclusion go to the same warp and run the
-    // same candidate sequence.  A warp packs the holes of its words into batches of up
-    // to 32, one hole per lane.
+    // ---- P3b: fill of the interior holes.  Work units are segments of kSeg words of a
+    // band row, taken by warps from a shared counter, so that busy rows spread over the
+    // warps while the holes of one disocclusion stay together.  A warp reads one word per
+    // lane and packs one-pixel cracks and wider holes into two separate batches of up to
+    // 32, one hole per lane, so that the lanes of a batch run the same code.
     {
-        const int nhw = ((y1 - y0) * nwords + 31) >> 5;
-        // lane L counts the flagged words among hword[L], hword[L + 32], ...
-        int mine = 0;
-        for (int i = lane; i < nhw; i += 32) mine += __popc(hword[i]);
-        int total = mine;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) total += __shfl_xor_sync(0xffffffffu, total, o);
-        const int r0 = (int)(((long long)total * warp) / NW), r1 = (int)(((long long)total * (warp + 1)) / NW);
-        int hx = 0, hv = 0, cnt = 0;  // this lane's hole of the current batch, batch size
-        int base = 0;                 // flagged words before hword[i0 .. i0 + 31]
-        for (int i0 = 0; i0 < nhw && base < r1; i0 += 32) {
-            const uint32_t fw = (i0 + lane < nhw) ? hword[i0 + lane] : 0u;
-            const int c = __popc(fw);
-            int incl = c;  // inclusive prefix over lanes
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int t = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += t;
-            }
-            const int excl = base + incl - c;
-            const int seg_total = __shfl_sync(0xffffffffu, incl, 31);
-            // this lane's flags have ranks excl .. excl + c - 1 (lowest bit first); keep
-            // those with rank in [r0, r1)
-            uint32_t sel = 0u;
-            {
-                const int first = max(r0, excl), last = min(r1, excl + c);
-                if (first < last) {
-                    sel = fw;
-                    for (int z = excl; z < first; ++z) sel &= sel - 1u;  // drop ranks below r0
-                    uint32_t rest = sel;                                 // drop ranks from r1 on
-                    for (int z = first; z < last; ++z) rest &= rest - 1u;
-                    sel &= ~rest;
+        constexpr int kSeg = 16;
+        const int nseg = (nwords + kSeg - 1) / kSeg;
+        const int nunits = (y1 - y0) * nseg;
+        int cx = 0, cv = 0, ccnt = 0;  // crack batch: this lane's pixel, batch size
+        int gx = 0, gv = 0, gcnt = 0;  // general batch
+        for (;;) {
+            int unit = 0;
+            if (lane == 0) unit = atomicAdd(ctr, 1);
+            unit = __shfl_sync(0xffffffffu, unit, 0);
+            if (unit >= nunits) break;
+            const int vj = unit / nseg;
+            const int g0 = (unit - vj * nseg) * kSeg;
+            const int v = y0 + vj;
+            const uint32_t* bv = bits + (size_t)(v - ra) * nwords;
+            const int last = lastr[vj];
+            const int g = g0 + lane;
+            const bool gin = lane < kSeg && g < nwords;
+            const uint32_t reach = gin ? bv[g] : 0u;
+            // interior holes: columns up to the last reached one
+            const int rem = last - (g << 5);
+            const uint32_t inb = rem >= 31 ? ~0u : (rem >= 0 ? ((2u << rem) - 1u) : 0u);
+            const uint32_t hw = gin ? (~reach & inb) : 0u;
+            // neighbour words for the crack test (the lanes beside, or memory at the segment ends)
+            uint32_t prev = __shfl_up_sync(0xffffffffu, reach, 1);
+            uint32_t next = __shfl_down_sync(0xffffffffu, reach, 1);
+            if (lane == 0) prev = g > 0 ? bv[g - 1] : 0u;
+            if (lane == kSeg - 1 || g + 1 >= nwords) next = (gin && g + 1 < nwords) ? bv[g + 1] : 0u;
+            const uint32_t left = (reach << 1) | (prev >> 31);   // bit i: column 32g + i - 1 reached
+            const uint32_t right = (reach >> 1) | (next << 31);  // bit i: column 32g + i + 1 reached
+            const uint32_t cm_l = hw & left & right;
+            const uint32_t gm_l = hw & ~cm_l;
+            uint32_t words = __ballot_sync(0xffffffffu, hw != 0u);
+            while (words) {
+                const int sl = __ffs(words) - 1;
+                words &= words - 1u;
+                const uint32_t cm = __shfl_sync(0xffffffffu, cm_l, sl);
+                const uint32_t gm = __shfl_sync(0xffffffffu, gm_l, sl);
+                const int wg = g0 + sl;
+                const int nc = __popc(cm), ng = __popc(gm);
+                if (ccnt + nc > 32) {
+                    if (lane < ccnt)
+                        f.out[(size_t)cv * w + cx] = fill_crack(cx, cv, ra, h, w, nwords, wpad, keys, bits);
+                    ccnt = 0;
                 }
-            }
-            uint32_t lanes = __ballot_sync(0xffffffffu, sel != 0u);
-            while (lanes) {
-                const int sl = __ffs(lanes) - 1;
-                lanes &= lanes - 1u;
-                uint32_t words = __shfl_sync(0xffffffffu, sel, sl);
-                while (words) {
-                    const int q = ((i0 + sl) << 5) + __ffs(words) - 1;
-                    words &= words - 1u;
-                    const int vj = q / nwords, g = q - vj * nwords;
-                    const int v = y0 + vj;
-                    const int rem = w - (g << 5);
-                    const uint32_t inb = rem >= 32 ? ~0u : ((1u << rem) - 1u);
-                    const uint32_t wm = ~bits[(size_t)(v - ra) * nwords + g] & inb;
-                    const int n = __popc(wm);
-                    if (cnt + n > 32) {  // flush the full batch
-                        if (lane < cnt)
-                            f.out[(size_t)hv * w + hx] = fill_pixel(hx, hv, ra, h, w, nwords, wpad, keys, bits);
-                        cnt = 0;
-                    }
-                    const int k = lane - cnt;
-                    if (k >= 0 && k < n) {
-                        hx = (g << 5) + nth_set_bit(wm, k);
-                        hv = v;
-                    }
-                    cnt += n;
+                if (gcnt + ng > 32) {
+                    const uint32_t o = fill_batch(gcnt, gx, gv, ra, h, w, nwords, wpad, keys, bits);
+                    if (lane < gcnt) f.out[(size_t)gv * w + gx] = o;
+                    gcnt = 0;
                 }
+                const int kc = lane - ccnt, kg = lane - gcnt;
+                if (kc >= 0 && kc < nc) {
+                    cx = (wg << 5) + nth_set_bit(cm, kc);
+                    cv = v;
+                }
+                if (kg >= 0 && kg < ng) {
+                    gx = (wg << 5) + nth_set_bit(gm, kg);
+                    gv = v;
+                }
+                ccnt += nc;
+                gcnt += ng;
             }
-            base += seg_total;
         }
-        if (lane < cnt) f.out[(size_t)hv * w + hx] = fill_pixel(hx, hv, ra, h, w, nwords, wpad, keys, bits);
+        if (lane < ccnt) f.out[(size_t)cv * w + cx] = fill_crack(cx, cv, ra, h, w, nwords, wpad, keys, bits);
+        {
+            const uint32_t o = fill_batch(gcnt, gx, gv, ra, h, w, nwords, wpad, keys, bits);
+            if (lane < gcnt) f.out[(size_t)gv * w + gx] = o;
+        }
     }
     __syncthreads();
 }
@@ -334,11 +402,12 @@ __global__ void __launch_bounds__(NT, MINB) fused_single(FrameArgs f, int wpad)
     const int slots = f.band + 2;
     unsigned long long* keys = reinterpret_cast<unsigned long long*>(smem_raw);
     uint32_t* bits = reinterpret_cast<uint32_t*>(smem_raw + (size_t)slots * wpad * 8);
-    uint32_t* hword = bits + (size_t)slots * ((wpad + 31) / 32);
+    int* ctr = reinterpret_cast<int*>(bits + (size_t)slots * ((wpad + 31) / 32));
+    int* lastr = ctr + 4;
     const int nbands = (f.h + f.band - 1) / f.band;
     for (int b = blockIdx.x; b < nbands; b += gridDim.x) {
         const int y0 = b * f.band;
-        run_band<NT>(f, y0, min(y0 + f.band, f.h), wpad, keys, bits, hword);
+        run_band<NT>(f, y0, min(y0 + f.band, f.h), wpad, keys, bits, ctr, lastr);
     }
 }
 
@@ -349,7 +418,8 @@ __global__ void __launch_bounds__(NT, MINB) fused_batch(const __grid_constant__ 
     const int slots = a.max_band + 2;
     unsigned long long* keys = reinterpret_cast<unsigned long long*>(smem_raw);
     uint32_t* bits = reinterpret_cast<uint32_t*>(smem_raw + (size_t)slots * wpad * 8);
-    uint32_t* hword = bits + (size_t)slots * ((wpad + 31) / 32);
+    int* ctr = reinterpret_cast<int*>(bits + (size_t)slots * ((wpad + 31) / 32));
+    int* lastr = ctr + 4;
     for (int item = blockIdx.x; item < a.total_items; item += gridDim.x) {
         int lo = 0, hi = a.n - 1;  // frame whose item range holds `item`
         while (lo < hi) {
@@ -359,7 +429,7 @@ __global__ void __launch_bounds__(NT, MINB) fused_batch(const __grid_constant__ 
         }
         const FrameArgs& f = a.f[lo];
         const int y0 = (item - a.item_start[lo]) * f.band;
-        run_band<NT>(f, y0, min(y0 + f.band, f.h), wpad, keys, bits, hword);
+        run_band<NT>(f, y0, min(y0 + f.band, f.h), wpad, keys, bits, ctr, lastr);
     }
 }
 
@@ -375,9 +445,9 @@ int fused_wpad(int w) { return ((w + 7) / 8) * 8; }
 size_t fused_smem_bytes(int wpad, int band)
 {
     const size_t slots = (size_t)band + 2;
-    // keys, reached bitmasks, and one flag bit per 32-pixel word of the band
-    return slots * (size_t)wpad * 8 + slots * (size_t)((wpad + 31) / 32) * 4 +
-           (((size_t)band * (size_t)((wpad + 31) / 32) + 31) / 32) * 4;
+    // keys, reached bitmasks, a work counter (16 bytes) and the last reached column of
+    // each band row
+    return slots * (size_t)wpad * 8 + slots * (size_t)((wpad + 31) / 32) * 4 + 16 + (size_t)band * 4;
 }
 
 cudaError_t fused_configure(int device, FusedLimits* lim)

@@ -99,6 +99,19 @@ struct FillAcc {
         wrem = __fsub_rn(wrem, wgt);
         return true;
     }
+    // add(rgba) when `take`, else nothing: a weight of exactly 0 leaves acc (acc + c*0)
+    // and wrem (wrem - 0) unchanged, so skipping and adding 0 are the same.
+    __device__ __forceinline__ void add_if(bool take, uint32_t rgba)
+    {
+        const float a = __fmul_rn(wrem, 0.5f);
+        const float b = __fmul_rn(__fmul_rn(0.3f, wrem), t);
+        const float wgt = take ? __fadd_rn(a, b) : 0.0f;
+        acc[0] = __fadd_rn(acc[0], __fmul_rn(__uint2float_rn(rgba & 255u), wgt));
+        acc[1] = __fadd_rn(acc[1], __fmul_rn(__uint2float_rn((rgba >> 8) & 255u), wgt));
+        acc[2] = __fadd_rn(acc[2], __fmul_rn(__uint2float_rn((rgba >> 16) & 255u), wgt));
+        acc[3] = __fadd_rn(acc[3], __fmul_rn(__uint2float_rn(rgba >> 24), wgt));
+        wrem = __fsub_rn(wrem, wgt);
+    }
     __device__ __forceinline__ bool any() const { return wrem != 1.0f; }
 
     // Exact early exit.  Every later step only grows acc and shrinks wrem: the updates
