@@ -324,7 +324,7 @@ __device__ __forceinline__ void run_band(const FrameArgs& f, int y0, int y1, int
     // lane and packs one-pixel cracks and wider holes into two separate batches of up to
     // 32, one hole per lane, so that the lanes of a batch run the same code.
     {
-        constexpr int kSeg = 16;
+        constexpr int kSeg = 8;
         const int nseg = (nwords + kSeg - 1) / kSeg;
         const int nunits = (y1 - y0) * nseg;
         int cx = 0, cv = 0, ccnt = 0;  // crack batch: this lane's pixel, batch size
@@ -524,8 +524,10 @@ cudaError_t fused_launch_batch(const BatchArgs& a, int wmax, const FusedLimits& 
     const int wpad = fused_wpad(wmax);
     const size_t smem = fused_smem_bytes(wpad, a.max_band);
     const bool two = 2 * (smem + 1024) <= (size_t)lim.smem_per_sm;
-    int grid = lim.sms * (two ? 2 : 1);
-    if (grid > a.total_items) grid = a.total_items;
+    // One CTA per (frame, band) item: the hardware block scheduler hands the next item to
+    // whichever SM frees up first, so bands with heavy disocclusions do not hold back the
+    // rest of the batch.
+    const int grid = a.total_items;
     if (grid < 1) return cudaSuccess;
     if (two)
         fused_batch<kSmall, 2><<<grid, kSmall, smem, stream>>>(a, wpad);
