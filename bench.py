@@ -51,6 +51,8 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=10.0, help="bounded CPU-oracle sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (profiling runs)")
+    p.add_argument("--workload", choices=["quest", "batch"], default="quest",
+                   help="quest: one 1832x1920 frame per step (the headline); batch: the 64-frame mixed batch")
     p.add_argument("--streams", type=int, default=4,
                    help="streams the steps are issued on, round-robin (frames overlap on the GPU)")
     return p.parse_args()
@@ -237,11 +239,76 @@ def run_reference(args, rank, world, budget_s: float = 120.0):
     print(json.dumps(line), flush=True)
 
 
+def run_batch(args):
+    """The batched workload: 64 frames (16 each of 1024x1024, 1440x1600, 1832x1920 and
+    2064x2208), each its own seeded scene, synthesized by one yoro_synthesize_batch launch
+    per step.  Two copies of the batch alternate so that consecutive steps touch
+    different memory (2 x 64 frames of inputs and outputs > 2x L2)."""
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+
+    import torch
+
+    import paper_2506_15183_gb300 as yoro
+    from paper_2506_15183_gb300 import scene
+
+    specs = scene.batch_configs(64)
+    with ProcessPoolExecutor(max_workers=min(16, os.cpu_count() or 2), mp_context=mp.get_context("spawn")) as ex:
+        data = list(ex.map(_render_left, specs))
+    copies = []
+    for _ in range(2):
+        frames = []
+        for (cfg, seed), (c, d) in zip(specs, data):
+            frames.append(dict(cfg.camera(), color=torch.from_numpy(c).cuda(), depth=torch.from_numpy(d).cuda(),
+                               out_color=torch.empty((cfg.h, cfg.w, 4), dtype=torch.uint8, device="cuda"),
+                               out_mask=torch.empty((cfg.h, cfg.w), dtype=torch.uint8, device="cuda")))
+        copies.append(frames)
+    npx = sum(cfg.w * cfg.h for cfg, _ in specs)
+    stream = torch.cuda.Stream()
+    for i in range(args.warmup):
+        yoro.yoro_synthesize_batch(copies[i % 2], stream=stream)
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for i in range(args.steps):
+        yoro.yoro_synthesize_batch(copies[i % 2], stream=stream)
+    ev1.record(stream)
+    stream.synchronize()
+    t_ms = ev0.elapsed_time(ev1)
+    secs = t_ms / 1e3
+    peak, _ = measured_peaks()
+    achieved = BYTES_PER_PIXEL * npx * args.steps / secs / 1e9
+    print(json.dumps({
+        "metric": "2nd-eye Mpix/s, batched workload (64 mixed frames per launch)", "value": round(npx * args.steps / secs / 1e6, 3),
+        "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_ms / args.steps, 4),
+        "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "batch: 16 each of 1024x1024, 1440x1600, 1832x1920, 2064x2208; 50-300 primitives; "
+                               "IPD U(0.055, 0.072) m; seeds 1000-1063", "frames_per_step": 64, "pixels_per_step": npx,
+                   "entry_point": "yoro_synthesize_batch"},
+        "frames_per_s": round(64 * args.steps / secs, 1),
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4)},
+    }), flush=True)
+
+
+def _render_left(spec):
+    from paper_2506_15183_gb300 import scene
+
+    cfg, seed = spec
+    c, d, _ = scene.render(cfg, seed, nthreads=2)
+    return c, d
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.workload == "batch":
+        if rank == 0:
+            run_batch(args)
         return
 
     import torch
