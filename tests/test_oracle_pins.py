@@ -125,6 +125,73 @@ def test_equal_depth_tie_goes_to_lowest_source_column():
     assert src.tolist() == [[-1, 0, -1]]
 
 
+def _rightmost_sources(xt):
+    """For every target of every row, the largest source column mapped there (-1: none)."""
+    h, w = xt.shape
+    right = np.full(h * w, -1, np.int64)
+    ys, xs = np.nonzero((xt >= 0) & (xt < w))
+    np.maximum.at(right, ys * w + xt[ys, xs], xs)
+    return right.reshape(h, w)
+
+
+def _hostile_depths(rng, h, w, zlo, zhi):
+    d = np.empty((h, w), np.float32)
+    for y in range(h):
+        x = 0
+        while x < w:
+            run = int(rng.integers(1, 30))
+            d[y, x : x + run] = rng.uniform(zlo, zhi)
+            x += run
+    d *= rng.uniform(0.97, 1.03, (h, w)).astype(np.float32)
+    flat = d.reshape(-1)
+    idx = rng.choice(flat.size, size=flat.size // 20, replace=False)
+    special = np.array([0.0, -0.0, -1.0, np.nan, np.inf, -np.inf, 1e-40, 1e-3, 1e7], np.float32)
+    flat[idx] = rng.choice(special, idx.size)
+    return d
+
+
+@pytest.mark.parametrize("case", range(8))
+def test_nearest_source_is_the_rightmost_one(case):
+    """Two sources of a row that reach the same target: the one further right is nearer.
+
+    With k = fx * ipd >= 0, Q = RN(k / zc) does not grow with zc, and floor(RN(x + 0.5 - Q))
+    rises by at least one per column for targets >= 0, so sources of equal clamped depth
+    never meet on a target and, where two meet, the right one has the larger Q, i.e. the
+    smaller depth.  The nearest-wins z-test of Alg. 2 therefore keeps the rightmost
+    source and its tie rule never decides.  Checked by brute force on the method's own
+    target columns: wide disparities, both clamps, invalid depths, repeated depths, and
+    depths whose disparity sits next to a rounding boundary of the target column.
+    """
+    rng = np.random.default_rng(900 + case)
+    h, w = 12, 301
+    fx, ipd, near, far = [(150.0, 0.063, 0.05, 1000.0), (8.0, 0.5, 0.05, 1000.0), (150.0, 0.3, 0.2, 5.0),
+                          (916.0, 0.063, 0.05, 1000.0)][case % 4]
+    if case < 4:
+        d = _hostile_depths(rng, h, w, 0.01, 60.0)
+    else:  # disparities k/z = n + 1/2 + tiny: targets next to a floor boundary
+        k = np.float32(fx) * np.float32(ipd)
+        n = rng.integers(0, 60, (h, w)).astype(np.float64)
+        eps = rng.choice(np.array([-1e-6, -1e-7, 0.0, 1e-7, 1e-6]), (h, w))
+        d = (float(k) / (n + 0.5 + eps)).astype(np.float32)
+        d[:, ::17] = d[:, 1::17][:, : d[:, ::17].shape[1]]  # repeated depths side by side
+    xt, zc = oracle.disparity(d, fx, ipd, near, far)
+    src, _ = oracle.forward_warp(xt, zc)
+    assert np.array_equal(src, _rightmost_sources(xt))
+    for y in range(h):  # equal clamped depth never shares a target
+        ok = (xt[y] >= 0) & (xt[y] < w)
+        pairs = set(zip(xt[y][ok].tolist(), zc[y][ok].view(np.uint32).tolist()))
+        assert len(pairs) == int(ok.sum())
+
+
+def test_nearest_source_is_the_rightmost_one_on_the_workload():
+    """The same property on a 1832x1920 frame of the scene generator (200 primitives)."""
+    cfg = scene.quest_config()
+    _, d, _ = scene.render(cfg, 2)
+    xt, zc = oracle.disparity(d, cfg.fx, cfg.ipd, cfg.near, cfg.far)
+    src, _ = oracle.forward_warp(xt, zc)
+    assert np.array_equal(src, _rightmost_sources(xt))
+
+
 # ----------------------------------------------------------------------------- hole edges
 @pytest.mark.parametrize("seed", range(4))
 def test_hole_edges_brute_force(seed):
