@@ -1,23 +1,27 @@
 // Fused second-eye synthesis kernel for GB300 (sm_103a).
 //
 // One CTA synthesizes a band of B output rows at once; shared memory holds the
-// band's warped rows plus one halo row above and below (rows y0-1 .. y0+B), each as
-// 64-bit z-buffer keys that become (depth, RGBA8) pairs.  Four steps, three CTA
+// band's warped rows plus one halo row above and below (the window, rows
+// y0-1 .. y0+B): per target pixel a 32-bit word that is first the source column and
+// then the depth, a 32-bit RGBA8 word, and a reached bit.  Four steps, three CTA
 // barriers per band:
 //
-//   0.  one thread starts 1-D bulk prefetches of the band's depth and color rows
-//       into L2 (cp.async.bulk.prefetch.L2), while all threads clear the keys;
+//   0.  one warp starts 1-D bulk prefetches of the window's depth and color rows
+//       into L2 (cp.async.bulk.prefetch.L2), while all threads clear the window;
 //   P1  disparity + forward warp (Alg. 1 closed form, Alg. 2 nearest kept): every
-//       source pixel of every row does a 64-bit atomicMin of
-//       (depth bits << 32 | source column) into its row's keys (O1: a row never
-//       writes another row);
-//   P2  resolve + gather: each key becomes (depth, RGBA8 of its source) in place;
-//       warp ballots write the rows' reached-pixel bitmasks;
-//   P3  the band's rows leave: reached pixels and the hole mask by 16-byte / 4-byte
-//       stores; holes are filled (Alg. 3, Eq. 6) by warps that take the band's
-//       32-pixel words round-robin, one hole per lane, so a wide disocclusion is
-//       spread over many warps.  Hole edges and kernel candidates come from the
-//       bitmasks (leading/trailing-zero counts over 32-pixel words).
+//       source pixel of every window row takes the atomic maximum of its source
+//       column into its target's word (O1: a row never writes another row).  In a
+//       row, of two sources that reach the same target the one further right is
+//       the nearer (see scatter_window), so the maximum column is the z-test's
+//       winner;
+//   P2  resolve + gather: each reached target loads its source's depth and color;
+//       warp ballots write the rows' reached-pixel bitmasks, and the band rows'
+//       reached pixels and hole mask leave for global memory at once;
+//   P3  holes right of a row's last reached pixel take the fallback; the other holes
+//       are filled (Alg. 3, Eq. 6) by warps that take segments of the band's rows from
+//       a shared counter, one hole per lane, so a wide disocclusion is spread over many
+//       warps.  Hole edges and kernel candidates come from the bitmasks
+//       (leading/trailing-zero counts over 32-pixel words).
 //
 // No thread ever waits on another CTA or on an asynchronous copy: the prefetches
 // only warm L2, and every read is an ordinary load.
@@ -39,12 +43,25 @@ __device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes)
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
+// The band window in shared memory.  Window row j (frame row ra + j) has its words at
+// zt + j*wpad (source column during P1, -1 for none; clamped depth bits of the source
+// after P2), rgba + j*wpad (color of the source after P2) and its reached bitmask at
+// bits + j*nwords.
+struct Window {
+    uint32_t* zt;
+    uint32_t* rgba;
+    uint32_t* bits;
+    int wpad, nwords, ra, slots;
+    __device__ __forceinline__ const uint32_t* zrow(int v) const { return zt + (v - ra) * wpad; }
+    __device__ __forceinline__ const uint32_t* crow(int v) const { return rgba + (v - ra) * wpad; }
+    __device__ __forceinline__ const uint32_t* brow(int v) const { return bits + (v - ra) * nwords; }
+};
+
 // Hole edges of pixel (v, x): L = highest reached column < x (or -1), R = lowest
 // reached column > x (or w), from the row's reached bitmask.
-__device__ __forceinline__ void find_edges(int x, int v, int ra, int nwords, const uint32_t* bits, int w, int& L,
-                                           int& R)
+__device__ __forceinline__ void find_edges(int x, int v, const Window& s, int w, int& L, int& R)
 {
-    const uint32_t* bv = bits + (size_t)(v - ra) * nwords;
+    const uint32_t* bv = s.brow(v);
     L = -1;
     {
         int wi = x >> 5;
@@ -67,20 +84,17 @@ __device__ __forceinline__ void find_edges(int x, int v, int ra, int nwords, con
                 R = (wi << 5) + __ffs(m) - 1;
                 break;
             }
-            if (++wi >= nwords) break;
+            if (++wi >= s.nwords) break;
             m = bv[wi];
         }
     }
 }
 
-// Hole fill of pixel (v, x) with edges L, R (R < w).  Rows of the band are addressed
-// relative to `ra`; rows outside [0, h) are skipped.  Pairs are (depth bits, rgba).
-__device__ __forceinline__ uint32_t fill_from_edges(int x, int v, int L, int R, int ra, int h, int w, int nwords,
-                                                    int wpad, const unsigned long long* keys, const uint32_t* bits)
+// Hole fill of pixel (v, x) with edges L, R (R < w).  Rows outside [0, h) are skipped.
+__device__ __forceinline__ uint32_t fill_from_edges(int x, int v, int L, int R, int h, int w, const Window& s)
 {
-    const uint2* pv = reinterpret_cast<const uint2*>(keys + (size_t)(v - ra) * wpad);
     const int wd = R - L;
-    const float d_occ = (L >= 0) ? __uint_as_float(pv[L].x) : 0.0f;
+    const float d_occ = (L >= 0) ? __uint_as_float(s.zrow(v)[L]) : 0.0f;
     FillAcc f;
     f.init(__fdiv_rn((float)(R - x), (float)wd));
     const int jhi = min(R + wd, w - 1);
@@ -90,8 +104,9 @@ __device__ __forceinline__ uint32_t fill_from_edges(int x, int v, int L, int R, 
 #pragma unroll 1
     for (int vv = v - 1; vv <= v + 1; ++vv) {
         if (vv < 0 || vv >= h) continue;
-        const uint32_t* b = bits + (size_t)(vv - ra) * nwords;
-        const uint2* p = reinterpret_cast<const uint2*>(keys + (size_t)(vv - ra) * wpad);
+        const uint32_t* b = s.brow(vv);
+        const uint32_t* zr = s.zrow(vv);
+        const uint32_t* cr = s.crow(vv);
 #pragma unroll 1
         for (int wi = whi; wi >= wlo; --wi) {
             uint32_t m = b[wi];
@@ -100,26 +115,25 @@ __device__ __forceinline__ uint32_t fill_from_edges(int x, int v, int L, int R, 
             while (m) {
                 const int bit = 31 - __clz(m);
                 m &= ~(1u << bit);
-                const uint2 q = p[(wi << 5) + bit];
-                if (__uint_as_float(q.x) < d_occ) continue;  // foreground (O2)
-                if (!f.add(q.y)) return f.result();          // weight reached exactly 0
+                const int c = (wi << 5) + bit;
+                if (__uint_as_float(zr[c]) < d_occ) continue;  // foreground (O2)
+                if (!f.add(cr[c])) return f.result();          // weight reached exactly 0
                 uint32_t out;
                 if (f.wrem <= kSettleFrom && f.settled(out)) return out;
             }
         }
     }
-    return f.any() ? f.result() : pv[R].y;
+    return f.any() ? f.result() : s.crow(v)[R];
 }
 
 // Fill of a batch of holes, one per lane below `cnt` (none on the image border).
-__device__ __forceinline__ uint32_t fill_batch(int cnt, int x, int v, int ra, int h, int w, int nwords, int wpad,
-                                               const unsigned long long* keys, const uint32_t* bits)
+__device__ __forceinline__ uint32_t fill_batch(int cnt, int x, int v, int h, int w, const Window& s)
 {
     uint32_t res = 0u;
     if ((int)(threadIdx.x & 31) < cnt) {
         int L, R;
-        find_edges(x, v, ra, nwords, bits, w, L, R);
-        res = fill_from_edges(x, v, L, R, ra, h, w, nwords, wpad, keys, bits);
+        find_edges(x, v, s, w, L, R);
+        res = fill_from_edges(x, v, L, R, h, w, s);
     }
     return res;
 }
@@ -130,32 +144,30 @@ __device__ __forceinline__ uint32_t fill_batch(int cnt, int x, int v, int ra, in
 // without early exits.  A slot that does not contribute (outside the image, a hole, or
 // nearer than the occluder) is given weight 0, which leaves acc and wrem unchanged
 // exactly, so the result equals the general loop's.
-__device__ __forceinline__ uint32_t fill_crack(int x, int v, int ra, int h, int w, int nwords, int wpad,
-                                               const unsigned long long* keys, const uint32_t* bits)
+__device__ __forceinline__ uint32_t fill_crack(int x, int v, int h, int w, const Window& s)
 {
-    const uint2* pv = reinterpret_cast<const uint2*>(keys + (size_t)(v - ra) * wpad);
-    const float d_occ = __uint_as_float(pv[x - 1].x);
+    const float d_occ = __uint_as_float(s.zrow(v)[x - 1]);
     FillAcc f;
     f.init(0.5f);
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         const int vv = v - 1 + k;
         const bool row_in = vv >= 0 && vv < h;
-        const int j = row_in ? vv - ra : v - ra;  // a valid row to read when vv is outside
-        const uint32_t* b = bits + (size_t)j * nwords;
-        const uint2* p = reinterpret_cast<const uint2*>(keys + (size_t)j * wpad);
+        const int vr = row_in ? vv : v;  // a valid row to read when vv is outside
+        const uint32_t* b = s.brow(vr);
+        const uint32_t* zr = s.zrow(vr);
+        const uint32_t* cr = s.crow(vr);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             const int col = x + 3 - c;
             const bool col_in = col < w;
             const int cc = col_in ? col : x + 1;
             const bool reached = (b[cc >> 5] >> (cc & 31)) & 1u;
-            const uint2 q = p[cc];
-            const bool contributes = row_in && col_in && reached && !(__uint_as_float(q.x) < d_occ);
-            f.add_if(contributes, q.y);
+            const bool contributes = row_in && col_in && reached && !(__uint_as_float(zr[cc]) < d_occ);
+            f.add_if(contributes, cr[cc]);
         }
     }
-    return f.any() ? f.result() : pv[x + 1].y;
+    return f.any() ? f.result() : s.crow(v)[x + 1];
 }
 
 // Position of the k-th (0-based) set bit of m; m must have more than k set bits.
@@ -175,21 +187,156 @@ __device__ __forceinline__ int nth_set_bit(uint32_t m, int k)
     return pos;
 }
 
-// One band [y0, y1) of one frame; shared memory holds rows ra..rb (ra = y0-1 or 0,
-// rb = y1 or h-1), row j at keys + j*wpad and bits + j*nwords.  Warp `warp` owns the
-// 32-pixel columns x = warp*32 + lane (+ NT, + 2*NT, ...) of every row in P1 and P2.
-// Ends with a barrier, so the next band may reuse shared memory.
+// Next item of a flat (row, column) enumeration dealt round-robin: advance by `dq`
+// columns and `dr` rows (the stride split as rows and a remainder), carrying a row.
+__device__ __forceinline__ void advance(int& r, int& q, int dr, int dq, int n)
+{
+    q += dq;
+    r += dr;
+    if (q >= n) {
+        q -= n;
+        ++r;
+    }
+}
+
+// P1 (Alg. 1 closed form, Alg. 2 nearest kept) over the window's nr rows.
+//
+// Alg. 2 keeps, per target, the nearest source, on equal depth the one met first.  In
+// one row that is the source with the largest column: with k = fx * ipd >= 0,
+// Q = RN(k / zc) does not grow with the clamped depth zc, and the target
+// floor(RN(x + 0.5 - Q)) rises by at least one per column at fixed Q (for targets >= 0
+// every rounding step there is at most half a unit of 2^-12 or finer, and the
+// round-half-even choice is the same one column apart).  So if sources x1 < x2 reach
+// one target, Q1 < Q2, i.e. zc1 > zc2: the right one is strictly nearer, and equal
+// depths never meet.  Each source therefore takes an atomic maximum of its column into
+// its target's word (one native 32-bit shared atomic), and the depth is fetched for
+// the winner alone in P2.
+//
+// The window's rows are contiguous in memory, so its pixels are enumerated in memory
+// order and dealt round-robin over the threads (consecutive lanes, consecutive
+// columns); each thread issues the loads of U pixels before it processes any.
 template <int NT>
-__device__ __forceinline__ void run_band(const FrameArgs& f, int y0, int y1, int wpad,
-                                         unsigned long long* keys, uint32_t* bits, int* ctr, int* lastr)
+__device__ __forceinline__ void scatter_window(const FrameArgs& f, const float* depth, int nr, int* src, int wpad)
+{
+    constexpr int U = 8;
+    const int w = f.w;
+    const int n = nr * w;
+    const uint32_t near_m1 = __float_as_uint(f.near_) - 1u, far_m1 = __float_as_uint(f.far_) - 1u;
+    const int dr = NT / w, dq = NT - dr * w;
+    int r = (int)threadIdx.x / w, q = (int)threadIdx.x - r * w;
+    for (int i = threadIdx.x; i < n; i += U * NT) {
+        float z[U];
+        int ru[U], xu[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            ru[u] = r;
+            xu[u] = q;
+            z[u] = (i + u * NT < n) ? __ldg(depth + i + u * NT) : 0.0f;
+            advance(r, q, dr, dq, w);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (i + u * NT < n) {
+                uint32_t zb;
+                const int xt = disparity_target(z[u], __fadd_rn((float)xu[u], 0.5f), f.k, near_m1, far_m1, f.half_m,
+                                                zb);
+                if ((unsigned)xt < (unsigned)w) atomicMax(src + ru[u] * wpad + xt, xu[u]);
+            }
+        }
+    }
+}
+
+// P2 (resolve + gather) over the window: warp `warp` owns the 32-pixel words
+// g = warp, warp + NW, ... of every row and takes RB rows per batch.  A reached target
+// loads its source's depth (clamped as in P1) and color; ballots give the reached
+// bitmasks.  Band rows send their reached pixels and hole mask to global memory right
+// here; their holes are written in P3, which visits only the rows flagged here as
+// holding one.  The loads of a batch are unconditional (a hole
+// or a lane past the row end reads column 0, a batch row past the window reads the
+// last window row), so the batch has no branches around its loads.
+template <int NT>
+__device__ __forceinline__ void resolve_window(const FrameArgs& f, const float* depth, const uint32_t* color,
+                                               int nr, int y0, int y1, const Window& s, int* rowflag)
+{
+    constexpr int NW = NT / 32, RB = 8;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int w = f.w, nwords = s.nwords, wpad = s.wpad;
+    const uint32_t near_m1 = __float_as_uint(f.near_) - 1u, far_m1 = __float_as_uint(f.far_) - 1u;
+    const int jb0 = y0 - s.ra, jb1 = y1 - s.ra;  // band rows of the window: [jb0, jb1)
+    for (int g = warp; g < nwords; g += NW) {
+        const int x = (g << 5) + lane;
+        const bool xin = x < w;
+        const uint32_t inrow = (g == nwords - 1 && (w & 31)) ? (1u << (w & 31)) - 1u : ~0u;
+        for (int j0 = 0; j0 < nr; j0 += RB) {
+            const int nb = min(RB, nr - j0);  // rows of this batch (warp-uniform)
+            int sc[RB];
+            float zs[RB];
+            uint32_t cs[RB];
+            // offsets advance by one row stride per row: no multiplies in the batch
+            int so = j0 * wpad + x;  // shared-memory word of (row, x)
+            int go = j0 * w;         // global pixel offset of the row in the window
+#pragma unroll
+            for (int u = 0; u < RB; ++u) {
+                sc[u] = (u < nb && xin) ? (int)s.zt[so] : -1;
+                so += wpad;
+            }
+#pragma unroll
+            for (int u = 0; u < RB; ++u) {
+                const int o = go + max(sc[u], 0);
+                zs[u] = 0.0f;
+                cs[u] = 0u;
+                if (u < nb) {
+                    zs[u] = __ldg(depth + o);
+                    cs[u] = __ldg(color + o);
+                }
+                go += w;
+            }
+            so = j0 * wpad + x;
+            int vo = (s.ra + j0) * w + x;  // frame pixel offset of (row, x)
+#pragma unroll
+            for (int u = 0; u < RB; ++u) {
+                if (u < nb) {
+                    const int j = j0 + u;
+                    const bool reached = sc[u] >= 0;
+                    const uint32_t m = __ballot_sync(0xffffffffu, reached);
+                    if (reached) {
+                        s.zt[so] = clamped_depth_bits(zs[u], near_m1, far_m1);
+                        s.rgba[so] = cs[u];
+                    }
+                    if (lane == 0) s.bits[j * nwords + g] = m;
+                    if (j >= jb0 && j < jb1) {
+                        if (lane == 0 && (~m & inrow)) rowflag[j] = 1;
+                        if (reached) f.out[vo] = cs[u];
+                        if (f.bulk) {  // four mask bytes per lane 0..7 (w % 4 == 0, mask 4-byte aligned)
+                            const uint32_t hn = (~m >> (lane << 2)) & 15u;
+                            if (lane < 8 && x - lane + (lane << 2) < w)
+                                *reinterpret_cast<uint32_t*>(f.mask + (vo - lane + (lane << 2))) =
+                                    (hn & 1u) | ((hn & 2u) << 7) | ((hn & 4u) << 14) | ((hn & 8u) << 21);
+                        } else if (xin) {
+                            f.mask[vo] = reached ? 0 : 1;
+                        }
+                    }
+                }
+                so += wpad;
+                vo += w;
+            }
+        }
+    }
+}
+
+// One band [y0, y1) of one frame; shared memory holds the window rows ra..rb
+// (ra = y0-1 or 0, rb = y1 or h-1).  Ends with a barrier, so the next band may reuse
+// shared memory.
+template <int NT>
+__device__ __forceinline__ void run_band(const FrameArgs& f, int y0, int y1, Window s, int* ctr, int* rowflag)
 {
     constexpr int NW = NT / 32;
-    constexpr int RB = 8;  // rows per batch of loads
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int w = f.w, h = f.h;
-    const int nwords = (w + 31) >> 5;
+    const int nwords = s.nwords;
     const int ra = max(y0 - 1, 0), rb = min(y1, h - 1);
     const int nr = rb - ra + 1;
+    s.ra = ra;
     const float* depth = f.depth + (size_t)ra * w;
     const uint32_t* color = f.color + (size_t)ra * w;
 
@@ -198,135 +345,70 @@ __device__ __forceinline__ void run_band(const FrameArgs& f, int y0, int y1, int
         for (int j = lane; j < nr; j += 32) prefetch_l2(color + (size_t)j * w, (uint32_t)w * 4u);
     }
     {
-        uint4* k4 = reinterpret_cast<uint4*>(keys);  // two keys per 16 bytes; wpad % 8 == 0
-        const int n4 = nr * (wpad >> 1);
+        uint4* z4 = reinterpret_cast<uint4*>(s.zt);  // four words per 16 bytes; wpad % 8 == 0
+        const int n4 = nr * (s.wpad >> 2);
         const uint4 e = make_uint4(~0u, ~0u, ~0u, ~0u);
-        for (int i = tid; i < n4; i += NT) k4[i] = e;
+        for (int i = tid; i < n4; i += NT) z4[i] = e;
+        for (int j = tid; j < nr; j += NT) rowflag[j] = 0;
         if (tid == 0) *ctr = 0;
     }
     __syncthreads();
 
     // ---- P1: disparity and nearest-wins scatter of rows ra..rb
-    for (int g = warp; g < nwords; g += NW) {
-        const int x = (g << 5) + lane;
-        const bool xin = x < w;
-        const float xc = __fadd_rn((float)x, 0.5f);
-        for (int j0 = 0; j0 < nr; j0 += RB) {
-            float z[RB];
-#pragma unroll
-            for (int u = 0; u < RB; ++u)
-                z[u] = (xin && j0 + u < nr) ? __ldg(depth + (size_t)(j0 + u) * w + x) : 0.0f;
-#pragma unroll
-            for (int u = 0; u < RB; ++u) {
-                if (xin && j0 + u < nr) {
-                    float zc;
-                    const int xt = disparity_target(z[u], xc, f.k, f.near_, f.far_, f.half_m, zc);
-                    if ((unsigned)xt < (unsigned)w) atomicMin(&keys[(size_t)(j0 + u) * wpad + xt], zkey(zc, x));
-                }
-            }
-        }
-    }
+    scatter_window<NT>(f, depth, nr, reinterpret_cast<int*>(s.zt), s.wpad);
     __syncthreads();
 
-    // ---- P2: resolve in place, gather colors, reached bitmasks
-    for (int g = warp; g < nwords; g += NW) {
-        const int x = (g << 5) + lane;
-        const bool xin = x < w;
-        for (int j0 = 0; j0 < nr; j0 += RB) {
-            uint2 kp[RB];  // (source column, depth bits) of each key
-            uint32_t rgba[RB];
-#pragma unroll
-            for (int u = 0; u < RB; ++u)
-                kp[u] = (xin && j0 + u < nr) ? reinterpret_cast<const uint2*>(keys + (size_t)(j0 + u) * wpad)[x]
-                                             : make_uint2(~0u, ~0u);
-#pragma unroll
-            for (int u = 0; u < RB; ++u)  // a key's high word is ~0 only while empty
-                rgba[u] = (kp[u].y != ~0u) ? __ldg(color + (size_t)(j0 + u) * w + kp[u].x) : 0u;
-#pragma unroll
-            for (int u = 0; u < RB; ++u) {
-                if (j0 + u < nr) {  // warp-uniform
-                    const bool reached = kp[u].y != ~0u;
-                    const uint32_t m = __ballot_sync(0xffffffffu, reached);
-                    if (lane == 0) bits[(size_t)(j0 + u) * nwords + g] = m;
-                    if (reached)
-                        reinterpret_cast<uint2*>(keys + (size_t)(j0 + u) * wpad)[x] = make_uint2(kp[u].y, rgba[u]);
-                }
-            }
-        }
-    }
+    // ---- P2: resolve, gather depths and colors, reached bitmasks; band rows' reached
+    // pixels and hole mask leave
+    resolve_window<NT>(f, depth, color, nr, y0, y1, s, rowflag);
     __syncthreads();
 
-    // Last reached column of every band row: holes right of it have no background edge
-    // (R = W) and take the fallback, the color of that last reached pixel (zero if the row
-    // has none).  They leave with the reached pixels; the fill below skips them.
-    for (int vj = warp; vj < y1 - y0; vj += NW) {
-        const uint32_t* bv = bits + (size_t)(vj + y0 - ra) * nwords;
+    // ---- P3a: per band row that holds a hole (one warp per row): its last reached
+    // column.  Holes right of it have no background edge (R = W) and take the fallback,
+    // the color of that last reached pixel (zero if the row has none), written here.
+    // Warp 0 also lists the rows that hold a hole.
+    const int nb = y1 - y0;
+    const int* bflag = rowflag + (y0 - ra);  // has-holes flags of the band rows
+    int* lastr = rowflag + s.slots;          // last reached column of band row vj
+    int* rowlist = lastr + s.slots;          // band rows that hold a hole
+    for (int vj = warp; vj < nb; vj += NW) {
+        if (!bflag[vj]) continue;
+        const int v = y0 + vj;
+        const uint32_t* bv = s.brow(v);
         int last = -1;
-        for (int g = lane; g < nwords; g += 32)
-            if (bv[g]) last = (g << 5) + 31 - __clz(bv[g]);
+        for (int gg = lane; gg < nwords; gg += 32) {
+            const uint32_t b = bv[gg];
+            if (b) last = (gg << 5) + 31 - __clz(b);
+        }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) last = max(last, __shfl_xor_sync(0xffffffffu, last, o));
+        const uint32_t border = last >= 0 ? s.crow(v)[last] : 0u;
+        uint32_t* orow = f.out + (size_t)v * w;
+        for (int x = last + 1 + lane; x < w; x += 32) orow[x] = border;
         if (lane == 0) lastr[vj] = last;
+    }
+    if (warp == 0) {
+        int n = 0;
+        for (int c = 0; c < nb; c += 32) {
+            const bool fl = c + lane < nb && bflag[c + lane];
+            const uint32_t fm = __ballot_sync(0xffffffffu, fl);
+            if (fl) rowlist[n + __popc(fm & ((1u << lane) - 1u))] = c + lane;
+            n += __popc(fm);
+        }
+        if (lane == 0) ctr[1] = n;
     }
     __syncthreads();
 
-    // ---- P3a: reached pixels, border holes and the hole mask leave
-    for (int v = y0; v < y1; ++v) {
-        const int j = v - ra;
-        const uint32_t* bv = bits + (size_t)j * nwords;
-        const uint2* pv = reinterpret_cast<const uint2*>(keys + (size_t)j * wpad);
-        const int last = lastr[v - y0];
-        const uint32_t border = last >= 0 ? pv[last].y : 0u;
-        uint32_t* orow = f.out + (size_t)v * w;
-        uint8_t* mrow = f.mask + (size_t)v * w;
-        for (int x0 = tid << 2; x0 < w; x0 += NT * 4) {
-            const uint32_t nib = (bv[x0 >> 5] >> (x0 & 31)) & 15u;  // reached flags of x0..x0+3
-            if (f.bulk && x0 + 3 < w) {
-                const uint4 p01 = *reinterpret_cast<const uint4*>(pv + x0);
-                const uint4 p23 = *reinterpret_cast<const uint4*>(pv + x0 + 2);
-                uint4 o = make_uint4(p01.y, p01.w, p23.y, p23.w);
-                if (x0 + 0 > last) o.x = border;
-                if (x0 + 1 > last) o.y = border;
-                if (x0 + 2 > last) o.z = border;
-                if (x0 + 3 > last) o.w = border;
-                // bytes of interior holes are left to the fill
-                const uint32_t wr = nib | (x0 + 0 > last ? 1u : 0u) | (x0 + 1 > last ? 2u : 0u) |
-                                    (x0 + 2 > last ? 4u : 0u) | (x0 + 3 > last ? 8u : 0u);
-                if (wr == 15u) {
-                    *reinterpret_cast<uint4*>(orow + x0) = o;
-                } else {
-                    if (wr & 1u) orow[x0] = o.x;
-                    if (wr & 2u) orow[x0 + 1] = o.y;
-                    if (wr & 4u) orow[x0 + 2] = o.z;
-                    if (wr & 8u) orow[x0 + 3] = o.w;
-                }
-                const uint32_t hn = ~nib & 15u;
-                *reinterpret_cast<uint32_t*>(mrow + x0) =
-                    (hn & 1u) | ((hn & 2u) << 7) | ((hn & 4u) << 14) | ((hn & 8u) << 21);
-            } else {
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const int x = x0 + i;
-                    if (x < w) {
-                        const bool reached = (nib >> i) & 1u;
-                        if (reached) orow[x] = pv[x].y;
-                        else if (x > last) orow[x] = border;
-                        mrow[x] = reached ? 0 : 1;
-                    }
-                }
-            }
-        }
-    }
-
     // ---- P3b: fill of the interior holes.  Work units are segments of kSeg words of a
-    // band row, taken by warps from a shared counter, so that busy rows spread over the
-    // warps while the holes of one disocclusion stay together.  A warp reads one word per
-    // lane and packs one-pixel cracks and wider holes into two separate batches of up to
-    // 32, one hole per lane, so that the lanes of a batch run the same code.
+    // listed row, taken by warps from a shared counter, so that busy rows spread over
+    // the warps while the holes of one disocclusion stay together.  A warp reads one word
+    // per lane and packs one-pixel cracks and wider holes into two separate batches of up
+    // to 32, one hole per lane, so that the lanes of a batch run the same code.
     {
         constexpr int kSeg = 8;
-        const int nseg = (nwords + kSeg - 1) / kSeg;
-        const int nunits = (y1 - y0) * nseg;
+        int sh = 0;  // segments per row rounded up to a power of two
+        while ((kSeg << sh) < nwords) ++sh;
+        const int nunits = ctr[1] << sh;
         int cx = 0, cv = 0, ccnt = 0;  // crack batch: this lane's pixel, batch size
         int gx = 0, gv = 0, gcnt = 0;  // general batch
         for (;;) {
@@ -334,10 +416,10 @@ __device__ __forceinline__ void run_band(const FrameArgs& f, int y0, int y1, int
             if (lane == 0) unit = atomicAdd(ctr, 1);
             unit = __shfl_sync(0xffffffffu, unit, 0);
             if (unit >= nunits) break;
-            const int vj = unit / nseg;
-            const int g0 = (unit - vj * nseg) * kSeg;
+            const int vj = rowlist[unit >> sh];
+            const int g0 = (unit & ((1 << sh) - 1)) * kSeg;
             const int v = y0 + vj;
-            const uint32_t* bv = bits + (size_t)(v - ra) * nwords;
+            const uint32_t* bv = s.brow(v);
             const int last = lastr[vj];
             const int g = g0 + lane;
             const bool gin = lane < kSeg && g < nwords;
@@ -349,7 +431,7 @@ __device__ __forceinline__ void run_band(const FrameArgs& f, int y0, int y1, int
             // neighbour words for the crack test (the lanes beside, or memory at the segment ends)
             uint32_t prev = __shfl_up_sync(0xffffffffu, reach, 1);
             uint32_t next = __shfl_down_sync(0xffffffffu, reach, 1);
-            if (lane == 0) prev = g > 0 ? bv[g - 1] : 0u;
+            if (lane == 0) prev = (gin && g > 0) ? bv[g - 1] : 0u;
             if (lane == kSeg - 1 || g + 1 >= nwords) next = (gin && g + 1 < nwords) ? bv[g + 1] : 0u;
             const uint32_t left = (reach << 1) | (prev >> 31);   // bit i: column 32g + i - 1 reached
             const uint32_t right = (reach >> 1) | (next << 31);  // bit i: column 32g + i + 1 reached
@@ -364,12 +446,11 @@ __device__ __forceinline__ void run_band(const FrameArgs& f, int y0, int y1, int
                 const int wg = g0 + sl;
                 const int nc = __popc(cm), ng = __popc(gm);
                 if (ccnt + nc > 32) {
-                    if (lane < ccnt)
-                        f.out[(size_t)cv * w + cx] = fill_crack(cx, cv, ra, h, w, nwords, wpad, keys, bits);
+                    if (lane < ccnt) f.out[(size_t)cv * w + cx] = fill_crack(cx, cv, h, w, s);
                     ccnt = 0;
                 }
                 if (gcnt + ng > 32) {
-                    const uint32_t o = fill_batch(gcnt, gx, gv, ra, h, w, nwords, wpad, keys, bits);
+                    const uint32_t o = fill_batch(gcnt, gx, gv, h, w, s);
                     if (lane < gcnt) f.out[(size_t)gv * w + gx] = o;
                     gcnt = 0;
                 }
@@ -386,28 +467,42 @@ __device__ __forceinline__ void run_band(const FrameArgs& f, int y0, int y1, int
                 gcnt += ng;
             }
         }
-        if (lane < ccnt) f.out[(size_t)cv * w + cx] = fill_crack(cx, cv, ra, h, w, nwords, wpad, keys, bits);
+        if (lane < ccnt) f.out[(size_t)cv * w + cx] = fill_crack(cx, cv, h, w, s);
         {
-            const uint32_t o = fill_batch(gcnt, gx, gv, ra, h, w, nwords, wpad, keys, bits);
+            const uint32_t o = fill_batch(gcnt, gx, gv, h, w, s);
             if (lane < gcnt) f.out[(size_t)gv * w + gx] = o;
         }
     }
     __syncthreads();
 }
 
+// Shared-memory layout of a window of `slots` rows (see fused_smem_bytes).
+__device__ __forceinline__ Window window_layout(unsigned char* smem, int slots, int wpad, int w, int*& ctr,
+                                                int*& rowflag)
+{
+    Window s;
+    s.zt = reinterpret_cast<uint32_t*>(smem);
+    s.rgba = s.zt + slots * wpad;
+    s.bits = s.rgba + slots * wpad;
+    s.wpad = wpad;
+    s.nwords = (w + 31) >> 5;
+    s.ra = 0;
+    s.slots = slots;
+    ctr = reinterpret_cast<int*>(s.bits + slots * ((wpad + 31) / 32));
+    rowflag = ctr + 4;
+    return s;
+}
+
 template <int NT, int MINB>
 __global__ void __launch_bounds__(NT, MINB) fused_single(FrameArgs f, int wpad)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    const int slots = f.band + 2;
-    unsigned long long* keys = reinterpret_cast<unsigned long long*>(smem_raw);
-    uint32_t* bits = reinterpret_cast<uint32_t*>(smem_raw + (size_t)slots * wpad * 8);
-    int* ctr = reinterpret_cast<int*>(bits + (size_t)slots * ((wpad + 31) / 32));
-    int* lastr = ctr + 4;
+    int *ctr, *rowflag;
+    const Window s = window_layout(smem_raw, f.band + 2, wpad, f.w, ctr, rowflag);
     const int nbands = (f.h + f.band - 1) / f.band;
     for (int b = blockIdx.x; b < nbands; b += gridDim.x) {
         const int y0 = b * f.band;
-        run_band<NT>(f, y0, min(y0 + f.band, f.h), wpad, keys, bits, ctr, lastr);
+        run_band<NT>(f, y0, min(y0 + f.band, f.h), s, ctr, rowflag);
     }
 }
 
@@ -415,11 +510,6 @@ template <int NT, int MINB>
 __global__ void __launch_bounds__(NT, MINB) fused_batch(const __grid_constant__ BatchArgs a, int wpad)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    const int slots = a.max_band + 2;
-    unsigned long long* keys = reinterpret_cast<unsigned long long*>(smem_raw);
-    uint32_t* bits = reinterpret_cast<uint32_t*>(smem_raw + (size_t)slots * wpad * 8);
-    int* ctr = reinterpret_cast<int*>(bits + (size_t)slots * ((wpad + 31) / 32));
-    int* lastr = ctr + 4;
     for (int item = blockIdx.x; item < a.total_items; item += gridDim.x) {
         int lo = 0, hi = a.n - 1;  // frame whose item range holds `item`
         while (lo < hi) {
@@ -428,8 +518,10 @@ __global__ void __launch_bounds__(NT, MINB) fused_batch(const __grid_constant__ 
             else hi = mid - 1;
         }
         const FrameArgs& f = a.f[lo];
+        int *ctr, *rowflag;
+        const Window s = window_layout(smem_raw, a.max_band + 2, wpad, f.w, ctr, rowflag);
         const int y0 = (item - a.item_start[lo]) * f.band;
-        run_band<NT>(f, y0, min(y0 + f.band, f.h), wpad, keys, bits, ctr, lastr);
+        run_band<NT>(f, y0, min(y0 + f.band, f.h), s, ctr, rowflag);
     }
 }
 
@@ -445,9 +537,10 @@ int fused_wpad(int w) { return ((w + 7) / 8) * 8; }
 size_t fused_smem_bytes(int wpad, int band)
 {
     const size_t slots = (size_t)band + 2;
-    // keys, reached bitmasks, a work counter (16 bytes) and the last reached column of
-    // each band row
-    return slots * (size_t)wpad * 8 + slots * (size_t)((wpad + 31) / 32) * 4 + 16 + (size_t)band * 4;
+    // per pixel a source/depth word and a color word, reached bitmasks, two counters
+    // (16 bytes), and per window row a has-holes flag, a last reached column and a list
+    // entry
+    return slots * (size_t)wpad * 8 + slots * (size_t)((wpad + 31) / 32) * 4 + 16 + slots * 12;
 }
 
 cudaError_t fused_configure(int device, FusedLimits* lim)

@@ -27,9 +27,10 @@ __global__ void scatter_kernel(FrameArgs f, unsigned long long* __restrict__ zbu
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
         const int y = (int)(i / (size_t)f.w);
         const int x = (int)(i - (size_t)y * f.w);
-        float zc;
-        const int xt = disparity_target(f.depth[i], __fadd_rn((float)x, 0.5f), f.k, f.near_, f.far_, f.half_m, zc);
-        if (xt >= 0 && xt < f.w) atomicMin(&zbuf[(size_t)y * f.w + xt], zkey(zc, x));
+        uint32_t zb;
+        const int xt = disparity_target(f.depth[i], __fadd_rn((float)x, 0.5f), f.k, __float_as_uint(f.near_) - 1u,
+                                        __float_as_uint(f.far_) - 1u, f.half_m, zb);
+        if (xt >= 0 && xt < f.w) atomicMin(&zbuf[(size_t)y * f.w + xt], zkey(zb, x));
     }
 }
 

@@ -12,11 +12,6 @@ namespace yoro {
 
 constexpr unsigned long long kEmptyKey = ~0ull;
 
-// Alg. 1 with Eq. 5 in closed form (parallel-axis pinhole pair, baseline ipd along
-// +x, left eye as source):  zc = clamp(z, near, far) with non-positive or non-finite
-// depth treated as far;  target column floor((x + 0.5) - k / zc) with k = fx * ipd.
-// Returns the target column (any int; the caller drops it outside [0, w)) and
-// writes the clamped depth.  `xc` is the pixel centre x + 0.5.
 // rcp.approx.ftz: one MUFU op, within 1 ulp of 1/x for normal x (a denormal
 // input flushes to a zero divisor and gives +inf).  Every use below tolerates that
 // error and the flush through a checked margin.
@@ -38,11 +33,22 @@ static __device__ __noinline__ int exact_target(float xc, float k, float zc)
 
 static __device__ __noinline__ float exact_rint_quotient(float a, float b) { return rintf(__fdiv_rn(a, b)); }
 
+// Bits of zc = clamp(z, near, far), with a depth that is not a positive finite number
+// taken as far (Alg. 1's clamp to the camera planes).  Positive binary32 values order
+// like their bit patterns, so the clamp is an unsigned min and max on the bits;
+// subtracting 1 first moves +0 (bits 0) to the top of the unsigned range, where the
+// negative numbers, -0, the infinities and the NaNs already are, and all of them
+// clamp to far.  near_m1 / far_m1 are the bits of near / far minus 1.
+__device__ __forceinline__ uint32_t clamped_depth_bits(float z, uint32_t near_m1, uint32_t far_m1)
+{
+    return max(min(__float_as_uint(z) - 1u, far_m1), near_m1) + 1u;
+}
+
 // Alg. 1 with Eq. 5 in closed form (parallel-axis pinhole pair, baseline ipd along
 // +x, left eye as source):  zc = clamp(z, near, far) with non-positive or non-finite
 // depth treated as far;  target column floor((x + 0.5) - RN(k / zc)) with k = fx * ipd.
 // Returns the target column (any int; the caller drops it outside [0, w)) and
-// writes the clamped depth.  `xc` is the pixel centre x + 0.5.
+// writes the bits of the clamped depth.  `xc` is the pixel centre x + 0.5.
 //
 // Only the floor is needed, so the IEEE quotient is computed only when a cheaper
 // estimate cannot decide it.  With q = RN(k * rcp(zc)), |q - k/zc| <= 1.51 * 2^-23 k/zc
@@ -51,11 +57,11 @@ static __device__ __noinline__ float exact_rint_quotient(float a, float b) { ret
 // 0.5 - M with M = 2^-20 (w + 1.5 + k/near) * (1 + 2^-10) >= twice that distance plus
 // an absolute 2^-20 (which also covers flushed denormals), bounded on the host per
 // frame.  If frac(t') lies in (M, 1 - M), floor(t) == floor(t').
-__device__ __forceinline__ int disparity_target(float z, float xc, float k, float near_, float far_,
-                                                float half_m, float& zc)
+__device__ __forceinline__ int disparity_target(float z, float xc, float k, uint32_t near_m1, uint32_t far_m1,
+                                                float half_m, uint32_t& zbits)
 {
-    if (!(z > 0.0f && z < __int_as_float(0x7f800000))) z = far_;
-    zc = fminf(fmaxf(z, near_), far_);
+    zbits = clamped_depth_bits(z, near_m1, far_m1);
+    const float zc = __uint_as_float(zbits);
     const float tp = __fsub_rn(xc, __fmul_rn(k, rcp_approx(zc)));
     const float fl = floorf(tp);
     if (fabsf(__fsub_rn(__fsub_rn(tp, fl), 0.5f)) < half_m) return (int)fl;
@@ -66,9 +72,9 @@ __device__ __forceinline__ int disparity_target(float z, float xc, float k, floa
 // source column.  For positive floats the bit order is the value order, so the
 // smallest key is the nearest source and, on equal depth, the lowest column (the
 // first writer of the paper's left-to-right scan).
-__device__ __forceinline__ unsigned long long zkey(float zc, int x)
+__device__ __forceinline__ unsigned long long zkey(uint32_t zbits, int x)
 {
-    return ((unsigned long long)__float_as_uint(zc) << 32) | (unsigned)x;
+    return ((unsigned long long)zbits << 32) | (unsigned)x;
 }
 
 // Accumulator of the Patcher (Alg. 3) for one hole pixel.

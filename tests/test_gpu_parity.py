@@ -69,7 +69,9 @@ def _random_frame(h, w, seed, zlo=0.05, zhi=3.0, bad=True):
     if bad:
         flat = d.reshape(-1)
         idx = rng.choice(flat.size, size=max(1, flat.size // 50), replace=False)
-        flat[idx] = rng.choice(np.array([0.0, -1.0, np.nan, np.inf, 1e-6, 5e6], np.float32), idx.size)
+        special = np.array([0.0, -0.0, -1.0, np.nan, np.inf, -np.inf, 1e-6, 5e6, 1e-40], np.float32)
+        special = np.append(special, np.array([0xFFC00000], np.uint32).view(np.float32))  # negative NaN
+        flat[idx] = rng.choice(special, idx.size)
     c = rng.integers(0, 256, (h, w, 4), dtype=np.uint8)
     return c, d
 
@@ -109,7 +111,7 @@ def test_unfused_quest_bit_exact(yoro):
 
 
 @pytest.mark.parametrize("h,w", [(1, 1), (1, 7), (7, 1), (3, 5), (67, 253), (33, 129), (5, 128), (9, 132),
-                                 (2, 1832), (41, 1830), (17, 260)])
+                                 (2, 1832), (41, 1830), (17, 260), (11, 545), (6, 2500), (3, 1000)])
 def test_ragged_sizes_random_depth(yoro, h, w):
     """Sizes that are not multiples of the 32/128-pixel blocks or of 4; hostile depths."""
     c, d = _random_frame(h, w, seed=h * 7919 + w)
