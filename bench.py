@@ -21,6 +21,7 @@ import argparse
 import glob
 import hashlib
 import json
+import re
 import os
 import statistics
 import subprocess
@@ -83,10 +84,20 @@ def max_over_ranks(t_ms: float, world: int, device=None) -> float:
     return float(t.item())
 
 
+def _code_only(src: str) -> str:
+    """C/CUDA source without comments and blank space: what the compiler sees."""
+    src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", " ", src)
+    return " ".join(src.split())
+
+
 def csrc_digest() -> str:
+    """Digest of the kernel sources' code (comments and layout ignored), to tell whether
+    stored ncu counters still describe the kernel."""
     h = hashlib.sha256()
     for f in sorted(glob.glob(os.path.join(CSRC, "*"))):
-        h.update(open(f, "rb").read())
+        if os.path.isfile(f) and f.endswith((".cu", ".cuh", ".h")):
+            h.update(_code_only(open(f, encoding="utf-8").read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -36,7 +36,9 @@ namespace yoro {
 
 namespace {
 
-constexpr float kSettleFrom = 0.0009765625f;  // 2^-10: start testing the exact early exit
+// Remaining weight below which the exact early exit is tested after each contribution
+// (2^-10: measured fastest among 2^-10 .. 2^-15 on the 1832x1920 workload).
+constexpr float kSettleFrom = 0.0009765625f;
 
 __device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes)
 {
@@ -51,6 +53,7 @@ struct Window {
     uint32_t* zt;
     uint32_t* rgba;
     uint32_t* bits;
+    uint32_t* pre;  // band row vj's hole prefix sums per word at pre + vj*nwords
     int wpad, nwords, ra, slots;
     __device__ __forceinline__ const uint32_t* zrow(int v) const { return zt + (v - ra) * wpad; }
     __device__ __forceinline__ const uint32_t* crow(int v) const { return rgba + (v - ra) * wpad; }
@@ -126,18 +129,6 @@ __device__ __forceinline__ uint32_t fill_from_edges(int x, int v, int L, int R, 
     return f.any() ? f.result() : s.crow(v)[R];
 }
 
-// Fill of a batch of holes, one per lane below `cnt` (none on the image border).
-__device__ __forceinline__ uint32_t fill_batch(int cnt, int x, int v, int h, int w, const Window& s)
-{
-    uint32_t res = 0u;
-    if ((int)(threadIdx.x & 31) < cnt) {
-        int L, R;
-        find_edges(x, v, s, w, L, R);
-        res = fill_from_edges(x, v, L, R, h, w, s);
-    }
-    return res;
-}
-
 // Hole fill of a one-pixel crack (v, x): reached pixels at x-1 and x+1, so L = x-1,
 // R = x+1, w = 2 and t = 1/2.  The kernel is rows v-1, v, v+1 times columns
 // min(x+3, W-1) .. x+1; all nine slots are visited in the same order as fill_from_edges,
@@ -168,6 +159,24 @@ __device__ __forceinline__ uint32_t fill_crack(int x, int v, int h, int w, const
         }
     }
     return f.any() ? f.result() : s.crow(v)[x + 1];
+}
+
+// Interior holes of 32-pixel word g of a band row with reached bitmask bv and last
+// reached column `last`: one-pixel cracks (both neighbours reached) in cm, wider holes
+// in gm.  Holes right of `last` are border holes and in neither.
+__device__ __forceinline__ void hole_masks(const uint32_t* bv, int g, int nwords, int last, uint32_t& cm,
+                                           uint32_t& gm)
+{
+    const uint32_t reach = bv[g];
+    const uint32_t prev = g > 0 ? bv[g - 1] : 0u;
+    const uint32_t next = g + 1 < nwords ? bv[g + 1] : 0u;
+    const int rem = last - (g << 5);
+    const uint32_t inb = rem >= 31 ? ~0u : (rem >= 0 ? ((2u << rem) - 1u) : 0u);
+    const uint32_t hw = ~reach & inb;
+    const uint32_t left = (reach << 1) | (prev >> 31);   // bit i: column 32g + i - 1 reached
+    const uint32_t right = (reach >> 1) | (next << 31);  // bit i: column 32g + i + 1 reached
+    cm = hw & left & right;
+    gm = hw & ~cm;
 }
 
 // Position of the k-th (0-based) set bit of m; m must have more than k set bits.
@@ -204,9 +213,9 @@ __device__ __forceinline__ void advance(int& r, int& q, int dr, int dq, int n)
 // Alg. 2 keeps, per target, the nearest source, on equal depth the one met first.  In
 // one row that is the source with the largest column: with k = fx * ipd >= 0,
 // Q = RN(k / zc) does not grow with the clamped depth zc, and the target
-// floor(RN(x + 0.5 - Q)) rises by at least one per column at fixed Q (for targets >= 0
-// every rounding step there is at most half a unit of 2^-12 or finer, and the
-// round-half-even choice is the same one column apart).  So if sources x1 < x2 reach
+// floor(RN(x + 0.5 - Q)) rises by at least one per column at fixed Q (for targets in
+// [0, 2^22) the rounding unit is at most 1/2, and a round-half-even tie resolves the
+// same way one column apart).  So if sources x1 < x2 reach
 // one target, Q1 < Q2, i.e. zc1 > zc2: the right one is strictly nearer, and equal
 // depths never meet.  Each source therefore takes an atomic maximum of its column into
 // its target's word (one native 32-bit shared atomic), and the depth is fetched for
@@ -250,13 +259,12 @@ __device__ __forceinline__ void scatter_window(const FrameArgs& f, const float* 
 // g = warp, warp + NW, ... of every row and takes RB rows per batch.  A reached target
 // loads its source's depth (clamped as in P1) and color; ballots give the reached
 // bitmasks.  Band rows send their reached pixels and hole mask to global memory right
-// here; their holes are written in P3, which visits only the rows flagged here as
-// holding one.  The loads of a batch are unconditional (a hole
+// here; their holes are written in P3.  The loads of a batch are unconditional (a hole
 // or a lane past the row end reads column 0, a batch row past the window reads the
 // last window row), so the batch has no branches around its loads.
 template <int NT>
 __device__ __forceinline__ void resolve_window(const FrameArgs& f, const float* depth, const uint32_t* color,
-                                               int nr, int y0, int y1, const Window& s, int* rowflag)
+                                               int nr, int y0, int y1, const Window& s)
 {
     constexpr int NW = NT / 32, RB = 8;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -266,7 +274,6 @@ __device__ __forceinline__ void resolve_window(const FrameArgs& f, const float* 
     for (int g = warp; g < nwords; g += NW) {
         const int x = (g << 5) + lane;
         const bool xin = x < w;
-        const uint32_t inrow = (g == nwords - 1 && (w & 31)) ? (1u << (w & 31)) - 1u : ~0u;
         for (int j0 = 0; j0 < nr; j0 += RB) {
             const int nb = min(RB, nr - j0);  // rows of this batch (warp-uniform)
             int sc[RB];
@@ -304,17 +311,9 @@ __device__ __forceinline__ void resolve_window(const FrameArgs& f, const float* 
                         s.rgba[so] = cs[u];
                     }
                     if (lane == 0) s.bits[j * nwords + g] = m;
-                    if (j >= jb0 && j < jb1) {
-                        if (lane == 0 && (~m & inrow)) rowflag[j] = 1;
+                    if (j >= jb0 && j < jb1 && xin) {  // a band row: the pixel and its mask byte leave
                         if (reached) f.out[vo] = cs[u];
-                        if (f.bulk) {  // four mask bytes per lane 0..7 (w % 4 == 0, mask 4-byte aligned)
-                            const uint32_t hn = (~m >> (lane << 2)) & 15u;
-                            if (lane < 8 && x - lane + (lane << 2) < w)
-                                *reinterpret_cast<uint32_t*>(f.mask + (vo - lane + (lane << 2))) =
-                                    (hn & 1u) | ((hn & 2u) << 7) | ((hn & 4u) << 14) | ((hn & 8u) << 21);
-                        } else if (xin) {
-                            f.mask[vo] = reached ? 0 : 1;
-                        }
+                        f.mask[vo] = reached ? 0 : 1;
                     }
                 }
                 so += wpad;
@@ -328,7 +327,7 @@ __device__ __forceinline__ void resolve_window(const FrameArgs& f, const float* 
 // (ra = y0-1 or 0, rb = y1 or h-1).  Ends with a barrier, so the next band may reuse
 // shared memory.
 template <int NT>
-__device__ __forceinline__ void run_band(const FrameArgs& f, int y0, int y1, Window s, int* ctr, int* rowflag)
+__device__ __forceinline__ void run_band(const FrameArgs& f, int y0, int y1, Window s, int* ctr, int* rowinfo)
 {
     constexpr int NW = NT / 32;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -349,7 +348,6 @@ __device__ __forceinline__ void run_band(const FrameArgs& f, int y0, int y1, Win
         const int n4 = nr * (s.wpad >> 2);
         const uint4 e = make_uint4(~0u, ~0u, ~0u, ~0u);
         for (int i = tid; i < n4; i += NT) z4[i] = e;
-        for (int j = tid; j < nr; j += NT) rowflag[j] = 0;
         if (tid == 0) *ctr = 0;
     }
     __syncthreads();
@@ -360,117 +358,127 @@ __device__ __forceinline__ void run_band(const FrameArgs& f, int y0, int y1, Win
 
     // ---- P2: resolve, gather depths and colors, reached bitmasks; band rows' reached
     // pixels and hole mask leave
-    resolve_window<NT>(f, depth, color, nr, y0, y1, s, rowflag);
+    resolve_window<NT>(f, depth, color, nr, y0, y1, s);
     __syncthreads();
 
-    // ---- P3a: per band row that holds a hole (one warp per row): its last reached
-    // column.  Holes right of it have no background edge (R = W) and take the fallback,
-    // the color of that last reached pixel (zero if the row has none), written here.
-    // Warp 0 also lists the rows that hold a hole.
+    // ---- P3a: per band row (one warp per row; rows with every pixel reached are done):
+    // its last reached column, the border holes right of it, and per 32-pixel word the
+    // number of interior cracks and wider holes with their prefix sums within the row.  Border holes have no
+    // background edge (R = W) and take the fallback, the color of the last reached pixel
+    // (zero if the row has none).  Counts are packed as cracks | wider << 16: a band
+    // holds fewer than 2^16 pixels.
     const int nb = y1 - y0;
-    const int* bflag = rowflag + (y0 - ra);  // has-holes flags of the band rows
-    int* lastr = rowflag + s.slots;          // last reached column of band row vj
-    int* rowlist = lastr + s.slots;          // band rows that hold a hole
+    int* lastr = rowinfo;           // last reached column of band row vj
+    int* rowoff = lastr + s.slots;  // holes of the band rows before row vj
     for (int vj = warp; vj < nb; vj += NW) {
-        if (!bflag[vj]) continue;
+        uint32_t tot = 0u;
         const int v = y0 + vj;
         const uint32_t* bv = s.brow(v);
         int last = -1;
+        bool full = true;  // every pixel of the row reached
         for (int gg = lane; gg < nwords; gg += 32) {
             const uint32_t b = bv[gg];
             if (b) last = (gg << 5) + 31 - __clz(b);
+            const uint32_t inrow = (gg == nwords - 1 && (w & 31)) ? (1u << (w & 31)) - 1u : ~0u;
+            full = full && b == inrow;
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) last = max(last, __shfl_xor_sync(0xffffffffu, last, o));
-        const uint32_t border = last >= 0 ? s.crow(v)[last] : 0u;
-        uint32_t* orow = f.out + (size_t)v * w;
-        for (int x = last + 1 + lane; x < w; x += 32) orow[x] = border;
-        if (lane == 0) lastr[vj] = last;
-    }
-    if (warp == 0) {
-        int n = 0;
-        for (int c = 0; c < nb; c += 32) {
-            const bool fl = c + lane < nb && bflag[c + lane];
-            const uint32_t fm = __ballot_sync(0xffffffffu, fl);
-            if (fl) rowlist[n + __popc(fm & ((1u << lane) - 1u))] = c + lane;
-            n += __popc(fm);
+        if (!__all_sync(0xffffffffu, full)) {  // warp-uniform
+            const uint32_t border = last >= 0 ? s.crow(v)[last] : 0u;
+            uint32_t* orow = f.out + (size_t)v * w;
+            for (int x = last + 1 + lane; x < w; x += 32) orow[x] = border;
+            if (lane == 0) lastr[vj] = last;
+            uint32_t* pre = s.pre + vj * nwords;
+            for (int g0 = 0; g0 < nwords; g0 += 32) {
+                const int g = g0 + lane;
+                uint32_t c = 0u;
+                if (g < nwords) {
+                    uint32_t cm, gm;
+                    hole_masks(bv, g, nwords, last, cm, gm);
+                    c = (uint32_t)__popc(cm) | ((uint32_t)__popc(gm) << 16);
+                }
+                uint32_t sc = c;  // inclusive scan over the lanes
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t y = __shfl_up_sync(0xffffffffu, sc, o);
+                    if (lane >= o) sc += y;
+                }
+                if (g < nwords) pre[g] = tot + sc - c;
+                tot += __shfl_sync(0xffffffffu, sc, 31);
+            }
         }
-        if (lane == 0) ctr[1] = n;
+        if (lane == 0) rowoff[vj] = (int)tot;
+    }
+    __syncthreads();
+    if (warp == 0) {  // exclusive scan of the row totals; the band total goes to ctr[1]
+        uint32_t run = 0u;
+        for (int c0 = 0; c0 < nb; c0 += 32) {
+            const uint32_t c = c0 + lane < nb ? (uint32_t)rowoff[c0 + lane] : 0u;
+            uint32_t sc = c;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, sc, o);
+                if (lane >= o) sc += y;
+            }
+            if (c0 + lane < nb) rowoff[c0 + lane] = (int)(run + sc - c);
+            run += __shfl_sync(0xffffffffu, sc, 31);
+        }
+        if (lane == 0) ctr[1] = (int)run;
     }
     __syncthreads();
 
-    // ---- P3b: fill of the interior holes.  Work units are segments of kSeg words of a
-    // listed row, taken by warps from a shared counter, so that busy rows spread over
-    // the warps while the holes of one disocclusion stay together.  A warp reads one word
-    // per lane and packs one-pixel cracks and wider holes into two separate batches of up
-    // to 32, one hole per lane, so that the lanes of a batch run the same code.
+    // ---- P3b: fill of the interior holes (Alg. 3, Eq. 6).  The band's wider holes, then
+    // its cracks, in row-major order, are dealt in chunks of 32 (one hole per lane) to
+    // whichever warp takes the next chunk from a shared counter, so a wide disocclusion
+    // is spread over many warps and every batch but the last of each kind is full.  A
+    // lane finds its hole by binary search over the row and word prefix sums.
     {
-        constexpr int kSeg = 8;
-        int sh = 0;  // segments per row rounded up to a power of two
-        while ((kSeg << sh) < nwords) ++sh;
-        const int nunits = ctr[1] << sh;
-        int cx = 0, cv = 0, ccnt = 0;  // crack batch: this lane's pixel, batch size
-        int gx = 0, gv = 0, gcnt = 0;  // general batch
+        const uint32_t tot = (uint32_t)ctr[1];
+        const int tc = (int)(tot & 0xffffu), tg = (int)(tot >> 16);
+        const int ng = (tg + 31) >> 5, nchunks = ng + ((tc + 31) >> 5);
         for (;;) {
-            int unit = 0;
-            if (lane == 0) unit = atomicAdd(ctr, 1);
-            unit = __shfl_sync(0xffffffffu, unit, 0);
-            if (unit >= nunits) break;
-            const int vj = rowlist[unit >> sh];
-            const int g0 = (unit & ((1 << sh) - 1)) * kSeg;
-            const int v = y0 + vj;
-            const uint32_t* bv = s.brow(v);
-            const int last = lastr[vj];
-            const int g = g0 + lane;
-            const bool gin = lane < kSeg && g < nwords;
-            const uint32_t reach = gin ? bv[g] : 0u;
-            // interior holes: columns up to the last reached one
-            const int rem = last - (g << 5);
-            const uint32_t inb = rem >= 31 ? ~0u : (rem >= 0 ? ((2u << rem) - 1u) : 0u);
-            const uint32_t hw = gin ? (~reach & inb) : 0u;
-            // neighbour words for the crack test (the lanes beside, or memory at the segment ends)
-            uint32_t prev = __shfl_up_sync(0xffffffffu, reach, 1);
-            uint32_t next = __shfl_down_sync(0xffffffffu, reach, 1);
-            if (lane == 0) prev = (gin && g > 0) ? bv[g - 1] : 0u;
-            if (lane == kSeg - 1 || g + 1 >= nwords) next = (gin && g + 1 < nwords) ? bv[g + 1] : 0u;
-            const uint32_t left = (reach << 1) | (prev >> 31);   // bit i: column 32g + i - 1 reached
-            const uint32_t right = (reach >> 1) | (next << 31);  // bit i: column 32g + i + 1 reached
-            const uint32_t cm_l = hw & left & right;
-            const uint32_t gm_l = hw & ~cm_l;
-            uint32_t words = __ballot_sync(0xffffffffu, hw != 0u);
-            while (words) {
-                const int sl = __ffs(words) - 1;
-                words &= words - 1u;
-                const uint32_t cm = __shfl_sync(0xffffffffu, cm_l, sl);
-                const uint32_t gm = __shfl_sync(0xffffffffu, gm_l, sl);
-                const int wg = g0 + sl;
-                const int nc = __popc(cm), ng = __popc(gm);
-                if (ccnt + nc > 32) {
-                    if (lane < ccnt) f.out[(size_t)cv * w + cx] = fill_crack(cx, cv, h, w, s);
-                    ccnt = 0;
-                }
-                if (gcnt + ng > 32) {
-                    const uint32_t o = fill_batch(gcnt, gx, gv, h, w, s);
-                    if (lane < gcnt) f.out[(size_t)gv * w + gx] = o;
-                    gcnt = 0;
-                }
-                const int kc = lane - ccnt, kg = lane - gcnt;
-                if (kc >= 0 && kc < nc) {
-                    cx = (wg << 5) + nth_set_bit(cm, kc);
-                    cv = v;
-                }
-                if (kg >= 0 && kg < ng) {
-                    gx = (wg << 5) + nth_set_bit(gm, kg);
-                    gv = v;
-                }
-                ccnt += nc;
-                gcnt += ng;
+            int chunk = 0;
+            if (lane == 0) chunk = atomicAdd(ctr, 1);
+            chunk = __shfl_sync(0xffffffffu, chunk, 0);
+            if (chunk >= nchunks) break;
+            const bool wide = chunk < ng;  // warp-uniform
+            const int sh = wide ? 16 : 0;
+            const int idx = ((wide ? chunk : chunk - ng) << 5) + lane;
+            if (idx >= (wide ? tg : tc)) continue;
+            // band row: the last row whose offset is <= idx
+            int lo = 0, hi = nb - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if ((int)(((uint32_t)rowoff[mid] >> sh) & 0xffffu) <= idx) lo = mid;
+                else hi = mid - 1;
             }
-        }
-        if (lane < ccnt) f.out[(size_t)cv * w + cx] = fill_crack(cx, cv, h, w, s);
-        {
-            const uint32_t o = fill_batch(gcnt, gx, gv, h, w, s);
-            if (lane < gcnt) f.out[(size_t)gv * w + gx] = o;
+            const int vj = lo;
+            const int r = idx - (int)(((uint32_t)rowoff[vj] >> sh) & 0xffffu);
+            // word of the row: the last word whose prefix is <= r
+            const uint32_t* pre = s.pre + vj * nwords;
+            lo = 0;
+            hi = nwords - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if ((int)((pre[mid] >> sh) & 0xffffu) <= r) lo = mid;
+                else hi = mid - 1;
+            }
+            const int g = lo;
+            const int k = r - (int)((pre[g] >> sh) & 0xffffu);
+            const int v = y0 + vj;
+            uint32_t cm, gm;
+            hole_masks(s.brow(v), g, nwords, lastr[vj], cm, gm);
+            const int x = (g << 5) + nth_set_bit(wide ? gm : cm, k);
+            uint32_t o;
+            if (wide) {
+                int L, R;
+                find_edges(x, v, s, w, L, R);
+                o = fill_from_edges(x, v, L, R, h, w, s);
+            } else {
+                o = fill_crack(x, v, h, w, s);
+            }
+            f.out[(size_t)v * w + x] = o;
         }
     }
     __syncthreads();
@@ -478,7 +486,7 @@ __device__ __forceinline__ void run_band(const FrameArgs& f, int y0, int y1, Win
 
 // Shared-memory layout of a window of `slots` rows (see fused_smem_bytes).
 __device__ __forceinline__ Window window_layout(unsigned char* smem, int slots, int wpad, int w, int*& ctr,
-                                                int*& rowflag)
+                                                int*& rowinfo)
 {
     Window s;
     s.zt = reinterpret_cast<uint32_t*>(smem);
@@ -488,8 +496,9 @@ __device__ __forceinline__ Window window_layout(unsigned char* smem, int slots, 
     s.nwords = (w + 31) >> 5;
     s.ra = 0;
     s.slots = slots;
-    ctr = reinterpret_cast<int*>(s.bits + slots * ((wpad + 31) / 32));
-    rowflag = ctr + 4;
+    s.pre = s.bits + slots * ((wpad + 31) / 32);
+    ctr = reinterpret_cast<int*>(s.pre + slots * ((wpad + 31) / 32));
+    rowinfo = ctr + 4;
     return s;
 }
 
@@ -497,12 +506,12 @@ template <int NT, int MINB>
 __global__ void __launch_bounds__(NT, MINB) fused_single(FrameArgs f, int wpad)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    int *ctr, *rowflag;
-    const Window s = window_layout(smem_raw, f.band + 2, wpad, f.w, ctr, rowflag);
+    int *ctr, *rowinfo;
+    const Window s = window_layout(smem_raw, f.band + 2, wpad, f.w, ctr, rowinfo);
     const int nbands = (f.h + f.band - 1) / f.band;
     for (int b = blockIdx.x; b < nbands; b += gridDim.x) {
         const int y0 = b * f.band;
-        run_band<NT>(f, y0, min(y0 + f.band, f.h), s, ctr, rowflag);
+        run_band<NT>(f, y0, min(y0 + f.band, f.h), s, ctr, rowinfo);
     }
 }
 
@@ -518,10 +527,10 @@ __global__ void __launch_bounds__(NT, MINB) fused_batch(const __grid_constant__ 
             else hi = mid - 1;
         }
         const FrameArgs& f = a.f[lo];
-        int *ctr, *rowflag;
-        const Window s = window_layout(smem_raw, a.max_band + 2, wpad, f.w, ctr, rowflag);
+        int *ctr, *rowinfo;
+        const Window s = window_layout(smem_raw, a.max_band + 2, wpad, f.w, ctr, rowinfo);
         const int y0 = (item - a.item_start[lo]) * f.band;
-        run_band<NT>(f, y0, min(y0 + f.band, f.h), s, ctr, rowflag);
+        run_band<NT>(f, y0, min(y0 + f.band, f.h), s, ctr, rowinfo);
     }
 }
 
@@ -537,10 +546,10 @@ int fused_wpad(int w) { return ((w + 7) / 8) * 8; }
 size_t fused_smem_bytes(int wpad, int band)
 {
     const size_t slots = (size_t)band + 2;
-    // per pixel a source/depth word and a color word, reached bitmasks, two counters
-    // (16 bytes), and per window row a has-holes flag, a last reached column and a list
-    // entry
-    return slots * (size_t)wpad * 8 + slots * (size_t)((wpad + 31) / 32) * 4 + 16 + slots * 12;
+    // per pixel a source/depth word and a color word; per 32-pixel word a reached
+    // bitmask and a hole prefix sum; two counters (16 bytes); per window row a last
+    // reached column and a hole offset
+    return slots * (size_t)wpad * 8 + slots * (size_t)((wpad + 31) / 32) * 8 + 16 + slots * 8;
 }
 
 cudaError_t fused_configure(int device, FusedLimits* lim)
