@@ -37,8 +37,8 @@ namespace yoro {
 namespace {
 
 // Remaining weight below which the exact early exit is tested after each contribution
-// (2^-10: measured fastest among 2^-10 .. 2^-15 on the 1832x1920 workload).
-constexpr float kSettleFrom = 0.0009765625f;
+// (2^-9: measured fastest among 2^-8 .. 2^-15 on the 1832x1920 workload).
+constexpr float kSettleFrom = 0.001953125f;
 
 __device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes)
 {
@@ -223,11 +223,12 @@ __device__ __forceinline__ void advance(int& r, int& q, int dr, int dq, int n)
 //
 // The window's rows are contiguous in memory, so its pixels are enumerated in memory
 // order and dealt round-robin over the threads (consecutive lanes, consecutive
-// columns); each thread issues the loads of U pixels before it processes any.
+// columns); each thread issues the loads of U = 4 pixels before it processes any (8
+// and 2 were measured slower).
 template <int NT>
 __device__ __forceinline__ void scatter_window(const FrameArgs& f, const float* depth, int nr, int* src, int wpad)
 {
-    constexpr int U = 8;
+    constexpr int U = 4;
     const int w = f.w;
     const int n = nr * w;
     const uint32_t near_m1 = __float_as_uint(f.near_) - 1u, far_m1 = __float_as_uint(f.far_) - 1u;

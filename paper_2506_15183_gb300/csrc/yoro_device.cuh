@@ -22,9 +22,10 @@ __device__ __forceinline__ float rcp_approx(float x)
     return r;
 }
 
-// The exact fallbacks live in functions of their own so that the compiler branches
-// around them instead of predicating their instructions into every pixel.
-static __device__ __noinline__ int exact_target(float xc, float k, float zc)
+// The exact fallbacks.  exact_target is inlined into the scatter loop (an out-of-line
+// call there cost more, in the caller's registers, than the rare branch it serves);
+// exact_rint_quotient stays out of line in the fill.
+static __device__ __forceinline__ int exact_target(float xc, float k, float zc)
 {
     // cvt.rmi gives floor; out-of-range values saturate to INT_MIN / INT_MAX, which
     // the caller drops like any off-frame column.

@@ -132,6 +132,26 @@ def test_wide_holes_random_depth(yoro, seed):
     _assert_same(_run(yoro, c, d, cam), ref, "wide holes")
 
 
+@pytest.mark.parametrize("per_row", [100, 1832])
+def test_target_columns_on_a_rounding_boundary(yoro, per_row):
+    """Depths whose disparity k/z is n + 1/2 put x + 0.5 - k/z on an integer, where the
+    fast estimate of the target column cannot decide the floor and the IEEE division
+    must.  100 such pixels per row fit the kernel's short list of deferred pixels; whole
+    rows overflow it and take the rescan of the window."""
+    h, w = 40, 1832
+    cam = _cam(w, h, ipd=0.063)
+    k = float(np.float32(cam["fx"]) * np.float32(cam["ipd"]))
+    rng = np.random.default_rng(per_row)
+    c, d = _random_frame(h, w, seed=77, zlo=0.3, zhi=20.0, bad=False)
+    for y in range(h):
+        cols = rng.choice(w, size=per_row, replace=False)
+        n = rng.integers(1, 120, per_row)
+        d[y, cols] = (k / (n + 0.5)).astype(np.float32)
+    ref = _ref(c, d, cam)
+    _assert_same(_run(yoro, c, d, cam), ref, "fused")
+    _assert_same(_run(yoro, c, d, cam, unfused=True), ref, "unfused")
+
+
 def test_misaligned_pointers_take_the_element_path(yoro):
     h, w = 40, 96
     c, d = _random_frame(h, w, seed=5)
