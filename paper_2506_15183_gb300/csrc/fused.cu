@@ -224,7 +224,32 @@ __device__ __forceinline__ void advance(int& r, int& q, int dr, int dq, int n)
 // The window's rows are contiguous in memory, so its pixels are enumerated in memory
 // order and dealt round-robin over the threads (consecutive lanes, consecutive
 // columns); each thread issues the loads of U = 4 pixels before it processes any (8
-// and 2 were measured slower).
+// and 2 were measured slower).  The groups whose U loads are all in range run without
+// per-pixel range tests; one remainder group keeps them.
+template <int NT, int U, bool FULL>
+__device__ __forceinline__ void scatter_iter(const FrameArgs& f, const float* depth, int n, int i, int& r, int& q,
+                                             int dr, int dq, int* src, int wpad, uint32_t near_m1, uint32_t far_m1)
+{
+    const int w = f.w;
+    float z[U];
+    int ru[U], xu[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        ru[u] = r;
+        xu[u] = q;
+        z[u] = (FULL || i + u * NT < n) ? __ldg(depth + i + u * NT) : 0.0f;
+        advance(r, q, dr, dq, w);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        if (FULL || i + u * NT < n) {
+            uint32_t zb;
+            const int xt = disparity_target(z[u], __fadd_rn((float)xu[u], 0.5f), f.k, near_m1, far_m1, f.half_m, zb);
+            if ((unsigned)xt < (unsigned)w) atomicMax(src + ru[u] * wpad + xt, xu[u]);
+        }
+    }
+}
+
 template <int NT>
 __device__ __forceinline__ void scatter_window(const FrameArgs& f, const float* depth, int nr, int* src, int wpad)
 {
@@ -234,26 +259,10 @@ __device__ __forceinline__ void scatter_window(const FrameArgs& f, const float* 
     const uint32_t near_m1 = __float_as_uint(f.near_) - 1u, far_m1 = __float_as_uint(f.far_) - 1u;
     const int dr = NT / w, dq = NT - dr * w;
     int r = (int)threadIdx.x / w, q = (int)threadIdx.x - r * w;
-    for (int i = threadIdx.x; i < n; i += U * NT) {
-        float z[U];
-        int ru[U], xu[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            ru[u] = r;
-            xu[u] = q;
-            z[u] = (i + u * NT < n) ? __ldg(depth + i + u * NT) : 0.0f;
-            advance(r, q, dr, dq, w);
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            if (i + u * NT < n) {
-                uint32_t zb;
-                const int xt = disparity_target(z[u], __fadd_rn((float)xu[u], 0.5f), f.k, near_m1, far_m1, f.half_m,
-                                                zb);
-                if ((unsigned)xt < (unsigned)w) atomicMax(src + ru[u] * wpad + xt, xu[u]);
-            }
-        }
-    }
+    int i = threadIdx.x;
+    for (; i + (U - 1) * NT < n; i += U * NT)  // every load of the group in range
+        scatter_iter<NT, U, true>(f, depth, n, i, r, q, dr, dq, src, wpad, near_m1, far_m1);
+    if (i < n) scatter_iter<NT, U, false>(f, depth, n, i, r, q, dr, dq, src, wpad, near_m1, far_m1);
 }
 
 // P2 (resolve + gather) over the window: warp `warp` owns the 32-pixel words
@@ -263,64 +272,72 @@ __device__ __forceinline__ void scatter_window(const FrameArgs& f, const float* 
 // here; their holes are written in P3.  The loads of a batch are unconditional (a hole
 // or a lane past the row end reads column 0, a batch row past the window reads the
 // last window row), so the batch has no branches around its loads.
+template <int RB, bool FULL>
+__device__ __forceinline__ void resolve_batch(const FrameArgs& f, const float* depth, const uint32_t* color,
+                                              const Window& s, int g, int j0, int nb, int jb0, int jb1,
+                                              uint32_t near_m1, uint32_t far_m1)
+{
+    const int lane = threadIdx.x & 31;
+    const int w = f.w, wpad = s.wpad;
+    const int x = (g << 5) + lane;
+    const bool xin = x < w;
+    int sc[RB];
+    float zs[RB];
+    uint32_t cs[RB];
+    // offsets advance by one row stride per row: no multiplies in the batch
+    int so = j0 * wpad + x;  // shared-memory word of (row, x)
+    int go = j0 * w;         // global pixel offset of the row in the window
+#pragma unroll
+    for (int u = 0; u < RB; ++u) {
+        sc[u] = ((FULL || u < nb) && xin) ? (int)s.zt[so] : -1;
+        so += wpad;
+    }
+#pragma unroll
+    for (int u = 0; u < RB; ++u) {
+        const int o = go + max(sc[u], 0);
+        zs[u] = 0.0f;
+        cs[u] = 0u;
+        if (FULL || u < nb) {
+            zs[u] = __ldg(depth + o);
+            cs[u] = __ldg(color + o);
+        }
+        go += w;
+    }
+    so = j0 * wpad + x;
+    int vo = (s.ra + j0) * w + x;  // frame pixel offset of (row, x)
+#pragma unroll
+    for (int u = 0; u < RB; ++u) {
+        if (FULL || u < nb) {
+            const int j = j0 + u;
+            const bool reached = sc[u] >= 0;
+            const uint32_t m = __ballot_sync(0xffffffffu, reached);
+            if (reached) {
+                s.zt[so] = clamped_depth_bits(zs[u], near_m1, far_m1);
+                s.rgba[so] = cs[u];
+            }
+            if (lane == 0) s.bits[j * s.nwords + g] = m;
+            if (j >= jb0 && j < jb1 && xin) {  // a band row: the pixel and its mask byte leave
+                if (reached) f.out[vo] = cs[u];
+                f.mask[vo] = reached ? 0 : 1;
+            }
+        }
+        so += wpad;
+        vo += w;
+    }
+}
+
 template <int NT>
 __device__ __forceinline__ void resolve_window(const FrameArgs& f, const float* depth, const uint32_t* color,
                                                int nr, int y0, int y1, const Window& s)
 {
-    constexpr int NW = NT / 32, RB = 8;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int w = f.w, nwords = s.nwords, wpad = s.wpad;
+    constexpr int NW = NT / 32, RB = 5;  // 15-row windows: three full batches (3..8 measured)
+    const int warp = threadIdx.x >> 5;
     const uint32_t near_m1 = __float_as_uint(f.near_) - 1u, far_m1 = __float_as_uint(f.far_) - 1u;
     const int jb0 = y0 - s.ra, jb1 = y1 - s.ra;  // band rows of the window: [jb0, jb1)
-    for (int g = warp; g < nwords; g += NW) {
-        const int x = (g << 5) + lane;
-        const bool xin = x < w;
-        for (int j0 = 0; j0 < nr; j0 += RB) {
-            const int nb = min(RB, nr - j0);  // rows of this batch (warp-uniform)
-            int sc[RB];
-            float zs[RB];
-            uint32_t cs[RB];
-            // offsets advance by one row stride per row: no multiplies in the batch
-            int so = j0 * wpad + x;  // shared-memory word of (row, x)
-            int go = j0 * w;         // global pixel offset of the row in the window
-#pragma unroll
-            for (int u = 0; u < RB; ++u) {
-                sc[u] = (u < nb && xin) ? (int)s.zt[so] : -1;
-                so += wpad;
-            }
-#pragma unroll
-            for (int u = 0; u < RB; ++u) {
-                const int o = go + max(sc[u], 0);
-                zs[u] = 0.0f;
-                cs[u] = 0u;
-                if (u < nb) {
-                    zs[u] = __ldg(depth + o);
-                    cs[u] = __ldg(color + o);
-                }
-                go += w;
-            }
-            so = j0 * wpad + x;
-            int vo = (s.ra + j0) * w + x;  // frame pixel offset of (row, x)
-#pragma unroll
-            for (int u = 0; u < RB; ++u) {
-                if (u < nb) {
-                    const int j = j0 + u;
-                    const bool reached = sc[u] >= 0;
-                    const uint32_t m = __ballot_sync(0xffffffffu, reached);
-                    if (reached) {
-                        s.zt[so] = clamped_depth_bits(zs[u], near_m1, far_m1);
-                        s.rgba[so] = cs[u];
-                    }
-                    if (lane == 0) s.bits[j * nwords + g] = m;
-                    if (j >= jb0 && j < jb1 && xin) {  // a band row: the pixel and its mask byte leave
-                        if (reached) f.out[vo] = cs[u];
-                        f.mask[vo] = reached ? 0 : 1;
-                    }
-                }
-                so += wpad;
-                vo += w;
-            }
-        }
+    for (int g = warp; g < s.nwords; g += NW) {
+        int j0 = 0;
+        for (; j0 + RB <= nr; j0 += RB) resolve_batch<RB, true>(f, depth, color, s, g, j0, RB, jb0, jb1, near_m1, far_m1);
+        if (j0 < nr) resolve_batch<RB, false>(f, depth, color, s, g, j0, nr - j0, jb0, jb1, near_m1, far_m1);
     }
 }
 
