@@ -129,6 +129,61 @@ __device__ __forceinline__ uint32_t fill_from_edges(int x, int v, int L, int R, 
     return f.any() ? f.result() : s.crow(v)[R];
 }
 
+// Hole fill of the pixels x of one hole (row v, edges L, R with R < w), one per active
+// lane, by the whole warp.  The depth gate and the candidates are the same for every
+// pixel of the hole, so the warp tests 32 kernel columns at a time (ballot of the
+// contributing ones) and hands each contributor's color, in Alg. 3's order, to all
+// lanes; each lane accumulates it with its own t and stops at its own exact exit.  A
+// kernel full of foreground candidates is thus crossed 32 columns per step instead of
+// one candidate per step.
+__device__ __forceinline__ uint32_t fill_hole_warp(int x, bool act, int v, int L, int R, int h, int w,
+                                                   const Window& s)
+{
+    const int lane = threadIdx.x & 31;
+    const int wd = R - L;
+    const float d_occ = (L >= 0) ? __uint_as_float(s.zrow(v)[L]) : 0.0f;
+    FillAcc f;
+    f.init(__fdiv_rn((float)(R - (act ? x : L + 1)), (float)wd));
+    bool done = !act;
+    uint32_t res = 0u;
+    const int jhi = min(R + wd, w - 1);
+    const int jlast = min(v + 1, h - 1) - s.ra;
+    for (int j = max(v - 1, 0) - s.ra; j <= jlast; ++j) {
+        for (int c0 = jhi; c0 >= R; c0 -= 32) {
+            const int c = c0 - lane;  // lane 0 takes the farthest column of the group
+            bool contrib = false;
+            uint32_t col = 0u;
+            if (c >= R) {
+                const int i = j * s.wpad + c;
+                const bool reached = (s.bits[j * s.nwords + (c >> 5)] >> (c & 31)) & 1u;
+                contrib = reached && !(__uint_as_float(s.zt[i]) < d_occ);  // not foreground (O2)
+                if (contrib) col = s.rgba[i];
+            }
+            uint32_t cm = __ballot_sync(0xffffffffu, contrib);
+            while (cm) {  // contributors in kernel order
+                const int k = __ffs(cm) - 1;
+                cm &= cm - 1u;
+                const uint32_t cc = __shfl_sync(0xffffffffu, col, k);
+                if (!done) {
+                    if (!f.add(cc)) {  // weight reached exactly 0
+                        res = f.result();
+                        done = true;
+                    } else {
+                        uint32_t out;
+                        if (f.wrem <= kSettleFrom && f.settled(out)) {
+                            res = out;
+                            done = true;
+                        }
+                    }
+                }
+                if (__all_sync(0xffffffffu, done)) return res;
+            }
+        }
+    }
+    if (!done) res = f.any() ? f.result() : s.crow(v)[R];
+    return res;
+}
+
 // Hole fill of a one-pixel crack (v, x): reached pixels at x-1 and x+1, so L = x-1,
 // R = x+1, w = 2 and t = 1/2.  The kernel is rows v-1, v, v+1 times columns
 // min(x+3, W-1) .. x+1; all nine slots are visited in the same order as fill_from_edges,
@@ -463,40 +518,49 @@ __device__ __forceinline__ void run_band(const FrameArgs& f, int y0, int y1, Win
             const bool wide = chunk < ng;  // warp-uniform
             const int sh = wide ? 16 : 0;
             const int idx = ((wide ? chunk : chunk - ng) << 5) + lane;
-            if (idx >= (wide ? tg : tc)) continue;
-            // band row: the last row whose offset is <= idx
-            int lo = 0, hi = nb - 1;
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if ((int)(((uint32_t)rowoff[mid] >> sh) & 0xffffu) <= idx) lo = mid;
-                else hi = mid - 1;
+            const bool act = idx < (wide ? tg : tc);  // lane 0 is always active
+            int v = 0, x = 0;
+            if (act) {
+                // band row: the last row whose offset is <= idx
+                int lo = 0, hi = nb - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if ((int)(((uint32_t)rowoff[mid] >> sh) & 0xffffu) <= idx) lo = mid;
+                    else hi = mid - 1;
+                }
+                const int vj = lo;
+                const int r = idx - (int)(((uint32_t)rowoff[vj] >> sh) & 0xffffu);
+                // word of the row: the last word whose prefix is <= r
+                const uint32_t* pre = s.pre + vj * nwords;
+                lo = 0;
+                hi = nwords - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if ((int)((pre[mid] >> sh) & 0xffffu) <= r) lo = mid;
+                    else hi = mid - 1;
+                }
+                const int g = lo;
+                const int k = r - (int)((pre[g] >> sh) & 0xffffu);
+                v = y0 + vj;
+                uint32_t cm, gm;
+                hole_masks(s.brow(v), g, nwords, lastr[vj], cm, gm);
+                x = (g << 5) + nth_set_bit(wide ? gm : cm, k);
             }
-            const int vj = lo;
-            const int r = idx - (int)(((uint32_t)rowoff[vj] >> sh) & 0xffffu);
-            // word of the row: the last word whose prefix is <= r
-            const uint32_t* pre = s.pre + vj * nwords;
-            lo = 0;
-            hi = nwords - 1;
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if ((int)((pre[mid] >> sh) & 0xffffu) <= r) lo = mid;
-                else hi = mid - 1;
-            }
-            const int g = lo;
-            const int k = r - (int)((pre[g] >> sh) & 0xffffu);
-            const int v = y0 + vj;
-            uint32_t cm, gm;
-            hole_masks(s.brow(v), g, nwords, lastr[vj], cm, gm);
-            const int x = (g << 5) + nth_set_bit(wide ? gm : cm, k);
-            uint32_t o;
+            uint32_t o = 0u;
             if (wide) {
-                int L, R;
-                find_edges(x, v, s, w, L, R);
-                o = fill_from_edges(x, v, L, R, h, w, s);
-            } else {
+                int L = -1, R = 0;
+                if (act) find_edges(x, v, s, w, L, R);
+                // one hole for the whole chunk: its kernel is scanned once by the warp
+                const int v0 = __shfl_sync(0xffffffffu, v, 0), L0 = __shfl_sync(0xffffffffu, L, 0),
+                          R0 = __shfl_sync(0xffffffffu, R, 0);
+                if (__all_sync(0xffffffffu, !act || (v == v0 && L == L0 && R == R0)))
+                    o = fill_hole_warp(x, act, v0, L0, R0, h, w, s);
+                else if (act)
+                    o = fill_from_edges(x, v, L, R, h, w, s);
+            } else if (act) {
                 o = fill_crack(x, v, h, w, s);
             }
-            f.out[(size_t)v * w + x] = o;
+            if (act) f.out[(size_t)v * w + x] = o;
         }
     }
     __syncthreads();
