@@ -54,6 +54,7 @@ def parse():
     p.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (profiling runs)")
     p.add_argument("--workload", choices=["quest", "batch"], default="quest",
                    help="quest: one 1832x1920 frame per step (the headline); batch: the 64-frame mixed batch")
+    p.add_argument("--no-tune", action="store_true", help="batch workload: skip the band-height autotuner")
     p.add_argument("--streams", type=int, default=4,
                    help="streams the steps are issued on, round-robin (frames overlap on the GPU)")
     return p.parse_args()
@@ -276,6 +277,10 @@ def run_batch(args):
         copies.append(frames)
     npx = sum(cfg.w * cfg.h for cfg, _ in specs)
     stream = torch.cuda.Stream()
+    wmax = max(cfg.w for cfg, _ in specs)
+    yoro.yoro_reset_tuning()
+    band_default = yoro.yoro_batch_band(wmax)
+    band = band_default if args.no_tune else yoro.yoro_tune_batch(copies[0], reps=3, stream=stream)
     for i in range(args.warmup):
         yoro.yoro_synthesize_batch(copies[i % 2], stream=stream)
     torch.cuda.synchronize()
@@ -296,7 +301,8 @@ def run_batch(args):
         "higher_is_better": True, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "batch: 16 each of 1024x1024, 1440x1600, 1832x1920, 2064x2208; 50-300 primitives; "
                                "IPD U(0.055, 0.072) m; seeds 1000-1063", "frames_per_step": 64, "pixels_per_step": npx,
-                   "entry_point": "yoro_synthesize_batch"},
+                   "entry_point": "yoro_synthesize_batch", "band_rows": band, "band_rows_untuned": band_default,
+                   "tuned": not args.no_tune},
         "frames_per_s": round(64 * args.steps / secs, 1),
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4)},

@@ -135,6 +135,29 @@ yoro_status yoro_synthesize_host(yoro_handle h, const void* host_color_rgba8, co
 yoro_status yoro_synthesize_batch(int n, const yoro_frame* frames, void* cuda_stream);
 
 /*
+ * Autotuner of yoro_synthesize_batch (a library service; the paper has no counterpart).
+ * Runs the batch `frames` (same arguments and contract as yoro_synthesize_batch) at a few
+ * band heights (rows per work item: the tallest that fits shared memory for the widest
+ * frame, a few just below it, and about 3/4, 1/2, 1/3 and 1/4 of it; the shorter ones
+ * run two CTAs of 512 threads per SM), `reps` timed launches each after one untimed one
+ * (CUDA events on cuda_stream), and keeps the fastest for this device and this widest
+ * width: later yoro_synthesize_batch launches on the device whose widest frame has that
+ * width use it.  Writes the chosen band to *out_band (if not NULL).  Every candidate
+ * computes the same outputs, so the frames' outputs hold the result when it returns.
+ * Synchronises cuda_stream.  1 <= reps <= 1000, n >= 1 with at least one non-empty frame.
+ * Returns the errors of yoro_synthesize_batch; the tuned table is left unchanged on error.
+ */
+yoro_status yoro_tune_batch(int n, const yoro_frame* frames, int reps, void* cuda_stream, int* out_band);
+
+/* Rows per work item that yoro_synthesize_batch uses on the current device for a launch
+ * whose widest frame is w pixels: the tuned height, else the tallest that fits shared
+ * memory.  0 if w < 1, w > yoro_max_fused_width() or the device cannot be queried. */
+int yoro_batch_band(int w);
+
+/* Forget every tuned band height (all devices). */
+void yoro_reset_tuning(void);
+
+/*
  * Synchronise cuda_stream and report whether work on it failed: YORO_ECUDA if the
  * stream or the runtime reports a CUDA error, else YORO_OK.  h may be NULL (batch
  * launches have no handle).

@@ -17,7 +17,8 @@ __all__ = [
     "YoroError", "Synthesizer", "load_library", "yoro_create", "yoro_destroy", "yoro_synthesize",
     "yoro_synthesize_unfused", "yoro_synthesize_host", "yoro_synthesize_batch", "yoro_stream_status",
     "yoro_max_fused_width", "yoro_status_string", "yoro_last_create_error", "STATUS",
-    "yoro_synthesize_noalloc", "yoro_noalloc_max_pixels",
+    "yoro_synthesize_noalloc", "yoro_noalloc_max_pixels", "yoro_tune_batch", "yoro_batch_band",
+    "yoro_reset_tuning",
 ]
 
 _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "libyoro.so")
@@ -74,6 +75,12 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.yoro_synthesize_noalloc.restype = I
     lib.yoro_noalloc_max_pixels.argtypes = []
     lib.yoro_noalloc_max_pixels.restype = I
+    lib.yoro_tune_batch.argtypes = [I, ctypes.POINTER(_Frame), I, P, ctypes.POINTER(I)]
+    lib.yoro_tune_batch.restype = I
+    lib.yoro_batch_band.argtypes = [I]
+    lib.yoro_batch_band.restype = I
+    lib.yoro_reset_tuning.argtypes = []
+    lib.yoro_reset_tuning.restype = None
     _lib = lib
     return lib
 
@@ -165,9 +172,7 @@ def yoro_synthesize_host(h: _Handle, color, depth, out_color, out_mask, stream=N
     _check(load_library().yoro_synthesize_host(h.ptr, *p, _stream(stream)), "yoro_synthesize_host")
 
 
-def yoro_synthesize_batch(frames, stream=None) -> None:
-    """frames: sequence of dicts with keys w, h, fx, fy, cx, cy, ipd, near, far, color, depth,
-    out_color, out_mask (device tensors)."""
+def _frame_array(frames):
     arr = (_Frame * max(len(frames), 1))()
     for i, fr in enumerate(frames):
         w, hh = int(fr["w"]), int(fr["h"])
@@ -176,7 +181,32 @@ def yoro_synthesize_batch(frames, stream=None) -> None:
                         _dev_ptr(fr["depth"], torch.float32, (hh, w), "depth"),
                         _dev_ptr(fr["out_color"], torch.uint8, (hh, w, 4), "out_color"),
                         _dev_ptr(fr["out_mask"], torch.uint8, (hh, w), "out_hole_mask"))
+    return arr
+
+
+def yoro_synthesize_batch(frames, stream=None) -> None:
+    """frames: sequence of dicts with keys w, h, fx, fy, cx, cy, ipd, near, far, color, depth,
+    out_color, out_mask (device tensors)."""
+    arr = _frame_array(frames)
     _check(load_library().yoro_synthesize_batch(len(frames), arr, _stream(stream)), "yoro_synthesize_batch")
+
+
+def yoro_tune_batch(frames, reps: int = 3, stream=None) -> int:
+    """Time the batch at several band heights, keep the fastest for later batch launches of
+    the same widest width on this device, and return it (synchronises the stream)."""
+    arr = _frame_array(frames)
+    band = ctypes.c_int(0)
+    _check(load_library().yoro_tune_batch(len(frames), arr, int(reps), _stream(stream), ctypes.byref(band)),
+           "yoro_tune_batch")
+    return band.value
+
+
+def yoro_batch_band(w: int) -> int:
+    return load_library().yoro_batch_band(int(w))
+
+
+def yoro_reset_tuning() -> None:
+    load_library().yoro_reset_tuning()
 
 
 def yoro_synthesize_noalloc(w, h, fx, fy, cx, cy, ipd, near, far, color, depth, out_color, out_mask,

@@ -2,10 +2,15 @@
 // Declarations and the contract of every entry point are in include/yoro.h.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
+#include <utility>
+#include <vector>
 
 #include "yoro.h"
 #include "yoro_internal.h"
@@ -213,39 +218,61 @@ yoro_status yoro_synthesize_host(yoro_handle c, const void* hcolor, const float*
     return YORO_OK;
 }
 
-yoro_status yoro_synthesize_batch(int n, const yoro_frame* frames, void* stream)
+}  // extern "C"
+
+namespace {
+
+// Band heights chosen by yoro_tune_batch, per (device, widest frame width of a launch).
+std::mutex g_tune_mutex;
+std::map<std::pair<int, int>, int> g_tuned_band;
+
+// Rows per work item of a batch launch whose widest frame is wmax: the tuned height if
+// one was measured for this device and width, else the tallest that fits shared memory.
+int batch_band(int dev, const FusedLimits& lim, int wmax)
 {
-    if (n < 0 || (n > 0 && !frames)) return YORO_EINVAL;
-    if (n > 4096) return YORO_ETOOBIG;
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return YORO_ECUDA;
-    FusedLimits lim;
-    if (yoro::fused_configure(dev, &lim) != cudaSuccess) return YORO_ECUDA;
-    // Validate everything before launching anything.
+    const int bmax = yoro::fused_max_band(lim, wmax);
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    const auto it = g_tuned_band.find({dev, wmax});
+    if (it != g_tuned_band.end() && it->second >= 1 && it->second <= bmax) return it->second;
+    return bmax;
+}
+
+// Checks every frame of a batch (before anything is launched); returns the widest width.
+yoro_status batch_validate(int n, const yoro_frame* frames, const FusedLimits& lim, int* wmax_out)
+{
+    int wmax = 0;
     for (int i = 0; i < n; ++i) {
         const yoro_frame& fr = frames[i];
         if (!camera_ok(fr.w, fr.h, fr.fx, fr.fy, fr.cx, fr.cy, fr.ipd, fr.near_, fr.far_)) return YORO_EINVAL;
         if (fr.w > lim.max_width) return YORO_ETOOBIG;
         if ((size_t)fr.w * fr.h == 0) continue;
         FrameArgs f;
-        yoro_status st = make_frame(fr.w, fr.h, fr.fx * fr.ipd, fr.near_, fr.far_, fr.color, fr.depth,
-                                    fr.out_color, fr.out_hole_mask, &f);
+        const yoro_status st = make_frame(fr.w, fr.h, fr.fx * fr.ipd, fr.near_, fr.far_, fr.color, fr.depth,
+                                          fr.out_color, fr.out_hole_mask, &f);
         if (st != YORO_OK) return st;
+        wmax = std::max(wmax, fr.w);
     }
+    if (wmax_out) *wmax_out = wmax;
+    return YORO_OK;
+}
+
+// Launches validated frames, up to kMaxBatch per launch.  band_override > 0 sets the rows
+// per work item of every launch (it must fit the widest frame); 0 takes batch_band().
+yoro_status batch_launch(int n, const yoro_frame* frames, int dev, const FusedLimits& lim, int band_override,
+                         cudaStream_t stream)
+{
     yoro::BatchArgs* a = new (std::nothrow) yoro::BatchArgs;
     if (!a) return YORO_ENOMEM;
     yoro_status result = YORO_OK;
     int i = 0;
     while (i < n && result == YORO_OK) {
-        // One launch takes up to kMaxBatch frames; every band is as tall as the
-        // widest frame's rows allow in shared memory.
         int i1 = i, wmax = 0, cnt = 0;
         for (; i1 < n && cnt < yoro::kMaxBatch; ++i1) {
             if ((size_t)frames[i1].w * frames[i1].h == 0) continue;
             if (frames[i1].w > wmax) wmax = frames[i1].w;
             ++cnt;
         }
-        const int band = yoro::fused_max_band(lim, wmax);
+        const int band = band_override > 0 ? band_override : batch_band(dev, lim, wmax);
         a->n = 0;
         a->total_items = 0;
         a->max_band = band;
@@ -261,11 +288,106 @@ yoro_status yoro_synthesize_batch(int n, const yoro_frame* frames, void* stream)
             a->total_items += (f.h + f.band - 1) / f.band;
         }
         a->item_start[a->n] = a->total_items;
-        if (a->n > 0 && yoro::fused_launch_batch(*a, wmax, lim, (cudaStream_t)stream) != cudaSuccess)
-            result = YORO_ECUDA;
+        if (a->n > 0 && yoro::fused_launch_batch(*a, wmax, lim, stream) != cudaSuccess) result = YORO_ECUDA;
     }
     delete a;
     return result;
+}
+
+}  // namespace
+
+extern "C" {
+
+yoro_status yoro_synthesize_batch(int n, const yoro_frame* frames, void* stream)
+{
+    if (n < 0 || (n > 0 && !frames)) return YORO_EINVAL;
+    if (n > 4096) return YORO_ETOOBIG;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return YORO_ECUDA;
+    FusedLimits lim;
+    if (yoro::fused_configure(dev, &lim) != cudaSuccess) return YORO_ECUDA;
+    const yoro_status st = batch_validate(n, frames, lim, nullptr);  // before launching anything
+    if (st != YORO_OK) return st;
+    return batch_launch(n, frames, dev, lim, 0, (cudaStream_t)stream);
+}
+
+yoro_status yoro_tune_batch(int n, const yoro_frame* frames, int reps, void* stream, int* out_band)
+{
+    if (n <= 0 || !frames || reps < 1 || reps > 1000) return YORO_EINVAL;
+    if (n > 4096) return YORO_ETOOBIG;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return YORO_ECUDA;
+    FusedLimits lim;
+    if (yoro::fused_configure(dev, &lim) != cudaSuccess) return YORO_ECUDA;
+    int wmax = 0;
+    yoro_status st = batch_validate(n, frames, lim, &wmax);
+    if (st != YORO_OK) return st;
+    if (wmax == 0) return YORO_EINVAL;  // nothing to time
+    // Candidates: the tallest band, a few just below it, and fractions of it (the
+    // shorter ones fit two CTAs per SM and run the 512-thread shape).
+    const int bmax = yoro::fused_max_band(lim, wmax);
+    std::vector<int> cand = {bmax, bmax - 1, bmax - 2, (3 * bmax + 3) / 4, (bmax + 1) / 2, (bmax + 2) / 3,
+                             (bmax + 3) / 4};
+    std::sort(cand.begin(), cand.end());
+    cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        cudaGetLastError();
+        return YORO_ECUDA;
+    }
+    const cudaStream_t s = (cudaStream_t)stream;
+    int best = bmax;
+    float best_ms = 0.0f;
+    bool have = false;
+    for (const int band : cand) {
+        if (band < 1 || band > bmax) continue;
+        st = batch_launch(n, frames, dev, lim, band, s);  // warm-up
+        for (int r = 0; r < reps && st == YORO_OK; ++r) {
+            if (r == 0 && cudaEventRecord(e0, s) != cudaSuccess) st = YORO_ECUDA;
+            if (st == YORO_OK) st = batch_launch(n, frames, dev, lim, band, s);
+        }
+        float ms = 0.0f;
+        if (st == YORO_OK && (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                              cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+            st = YORO_ECUDA;
+        if (st != YORO_OK) break;
+        if (!have || ms < best_ms) {
+            best = band;
+            best_ms = ms;
+            have = true;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != YORO_OK) {
+        cudaGetLastError();
+        return st;
+    }
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        g_tuned_band[{dev, wmax}] = best;
+    }
+    if (out_band) *out_band = best;
+    return YORO_OK;
+}
+
+int yoro_batch_band(int w)
+{
+    int dev = 0;
+    FusedLimits lim;
+    if (w < 1 || cudaGetDevice(&dev) != cudaSuccess || yoro::fused_configure(dev, &lim) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    if (w > lim.max_width) return 0;
+    return batch_band(dev, lim, w);
+}
+
+void yoro_reset_tuning(void)
+{
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    g_tuned_band.clear();
 }
 
 yoro_status yoro_stream_status(yoro_handle c, void* stream)

@@ -76,6 +76,10 @@ def test_null_handle_and_strings(lib):
     assert lib.yoro_synthesize_unfused(None, None, None, None, None, None) == 1
     assert lib.yoro_synthesize_host(None, None, None, None, None, None) == 1
     assert lib.yoro_synthesize_batch(-1, None, None) == 1
+    assert lib.yoro_tune_batch(0, None, 1, None, None) == 1
+    assert lib.yoro_tune_batch(-3, None, 1, None, None) == 1
+    assert lib.yoro_batch_band(0) == 0
+    lib.yoro_reset_tuning()
     lib.yoro_destroy(None)
     for code in range(7):
         assert lib.yoro_status_string(code)

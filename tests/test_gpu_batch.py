@@ -90,3 +90,28 @@ def test_batch_replays_from_a_cuda_graph(batch64):
     g.replay()
     torch.cuda.synchronize()
     _check(sub)
+
+
+def test_tuned_band_is_used_and_stays_exact(batch64):
+    """The autotuner picks one of its candidate band heights for the widest frame, later
+    batch launches use it, results stay bit-exact, and a reset restores the default."""
+    yoro, frames = batch64
+    wmax = max(fr["w"] for fr in frames)
+    yoro.yoro_reset_tuning()
+    default = yoro.yoro_batch_band(wmax)
+    assert default >= 1
+    for fr in frames:
+        fr["out_color"].zero_()
+        fr["out_mask"].fill_(7)
+    band = yoro.yoro_tune_batch(frames, reps=2)
+    assert 1 <= band <= default
+    assert yoro.yoro_batch_band(wmax) == band
+    torch.cuda.synchronize()
+    _check(frames)  # the tuner's own launches already wrote the result
+    for fr in frames:
+        fr["out_color"].zero_()
+    yoro.yoro_synthesize_batch(frames)
+    torch.cuda.synchronize()
+    _check(frames)
+    yoro.yoro_reset_tuning()
+    assert yoro.yoro_batch_band(wmax) == default

@@ -152,6 +152,30 @@ def test_target_columns_on_a_rounding_boundary(yoro, per_row):
     _assert_same(_run(yoro, c, d, cam, unfused=True), ref, "unfused")
 
 
+@pytest.mark.parametrize("h,w", [(11000, 96), (5200, 768), (12000, 40)])
+def test_tall_bands(yoro, h, w):
+    """Narrow, tall frames give bands of more than 32 rows (several 32-row steps in the
+    per-row hole pass and in the fill's row search), on both launch shapes (one CTA per
+    SM, and two half-height CTAs per SM)."""
+    c, d = _random_frame(h, w, seed=h + w, zlo=0.05, zhi=30.0)
+    cam = _cam(w, h, fx=max(w / 2.0, 8.0), ipd=0.08)
+    _assert_same(_run(yoro, c, d, cam), _ref(c, d, cam), f"fused {h}x{w}")
+
+
+@pytest.mark.parametrize("fx,ipd,near,far", [(916.0, 0.063, 1e-4, 1000.0), (916.0, 0.5, 0.05, 2.0),
+                                             (5000.0, 0.063, 0.05, 1000.0), (916.0, 1e-6, 0.05, 1000.0)])
+def test_extreme_cameras(yoro, fx, ipd, near, far):
+    """Disparities up to millions of pixels (tiny near plane: every estimate undecided, the
+    IEEE division decides all of them), a near far plane that clamps most depths, a long
+    focal length, and a sub-pixel baseline."""
+    h, w = 48, 1832
+    c, d = _random_frame(h, w, seed=int(fx) + int(ipd * 1e3), zlo=0.01, zhi=50.0)
+    cam = dict(w=w, h=h, fx=fx, fy=fx, cx=w / 2.0, cy=h / 2.0, ipd=ipd, near=near, far=far)
+    ref = _ref(c, d, cam)
+    _assert_same(_run(yoro, c, d, cam), ref, "fused")
+    _assert_same(_run(yoro, c, d, cam, unfused=True), ref, "unfused")
+
+
 def test_misaligned_pointers_take_the_element_path(yoro):
     h, w = 40, 96
     c, d = _random_frame(h, w, seed=5)
