@@ -52,6 +52,10 @@ def _load():
         lib.oracle_fill.restype = None
         lib.oracle_synthesize.argtypes = [I, I, F, F, F, F, F, F, F, P, P, P, P]
         lib.oracle_synthesize.restype = I
+        lib.oracle_fill_ex.argtypes = [I, I, P, P, P, P, P, I, I, P]
+        lib.oracle_fill_ex.restype = None
+        lib.oracle_synthesize_ex.argtypes = [I, I, F, F, F, F, F, F, F, P, P, I, I, P, P]
+        lib.oracle_synthesize_ex.restype = I
         _lib = lib
     return _lib
 
@@ -103,8 +107,9 @@ def hole_edges(src):
     return L, R
 
 
-def fill(src, zt, L, R, warped):
-    """Algorithm 3 + Eq. 6 over every hole pixel: the final uint8[H,W,4] image."""
+def fill(src, zt, L, R, warped, kernel_rows=3, nearest_first=False):
+    """Algorithm 3 + Eq. 6 over every hole pixel: the final uint8[H,W,4] image.  kernel_rows
+    is the kernel height h (odd); nearest_first visits each row's columns from R up."""
     src = _c(src, np.int32)
     zt = _c(zt, np.float32)
     L = _c(L, np.int32)
@@ -112,12 +117,12 @@ def fill(src, zt, L, R, warped):
     warped = _c(warped, np.uint8)
     h, w = src.shape
     out = np.empty((h, w, 4), np.uint8)
-    _load().oracle_fill(w, h, src.ctypes.data, zt.ctypes.data, L.ctypes.data, R.ctypes.data,
-                        warped.ctypes.data, out.ctypes.data)
+    _load().oracle_fill_ex(w, h, src.ctypes.data, zt.ctypes.data, L.ctypes.data, R.ctypes.data,
+                           warped.ctypes.data, int(kernel_rows), int(bool(nearest_first)), out.ctypes.data)
     return out
 
 
-def synthesize(color, depth, fx, fy, cx, cy, ipd, near, far):
+def synthesize(color, depth, fx, fy, cx, cy, ipd, near, far, kernel_rows=3, nearest_first=False):
     """Left eye (color uint8[H,W,4], depth float32[H,W]) -> right eye (color, hole mask)."""
     color = _c(color, np.uint8)
     depth = _c(depth, np.float32)
@@ -126,8 +131,9 @@ def synthesize(color, depth, fx, fy, cx, cy, ipd, near, far):
         raise ValueError("color must be uint8[H,W,4] matching depth")
     out = np.empty((h, w, 4), np.uint8)
     mask = np.empty((h, w), np.uint8)
-    rc = _load().oracle_synthesize(w, h, fx, fy, cx, cy, ipd, near, far, color.ctypes.data,
-                                   depth.ctypes.data, out.ctypes.data, mask.ctypes.data)
+    rc = _load().oracle_synthesize_ex(w, h, fx, fy, cx, cy, ipd, near, far, color.ctypes.data,
+                                      depth.ctypes.data, int(kernel_rows), int(bool(nearest_first)),
+                                      out.ctypes.data, mask.ctypes.data)
     if rc != 0:
         raise RuntimeError(f"oracle_synthesize failed ({rc})")
     return out, mask

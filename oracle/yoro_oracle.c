@@ -28,6 +28,8 @@
  *   oracle_hole_edges    brute force nearest valid column on each side.
  *   oracle_fill          closed forms: one contributing candidate returns its color;
  *                        two contributors blend as c2 + (c1 - c2) / (1.5 - 0.3 t);
+ *                        the geometric closed form sum q^i c_i / sum q^i (exact
+ *                        rationals) for every kernel height and column order;
  *                        depth gate, kernel extent, row order and the fallback are
  *                        checked by hand-built cases.  Beyond those small cases the
  *                        fill on general inputs is parity unpinned: it follows the
@@ -174,10 +176,13 @@ void oracle_hole_edges(int w, int h, const int32_t* src, int32_t* L, int32_t* R)
  *   d_occ  = zt(v, L), or 0 if L = -1    depth of the occluding edge
  *   t      = (R - u) / w                 Eq. 6's (u - r_x) / r_z, distance from the
  *                                        background edge over the hole width
- *   kernel = rows v-1, v, v+1 (h = 3, rows outside the image skipped), and in each
- *            row the w + 1 columns from min(R + w, w_img - 1) down to R: the
- *            background side, farthest column first, as Algorithm 3's kernel runs
- *            from r.x - r.z up to r.x in the paper's frame.
+ *   kernel = rows v-1, v, v+1 (h = 3, the paper's default height; rows outside the
+ *            image skipped), and in each row the w + 1 columns from
+ *            min(R + w, w_img - 1) down to R: the background side, farthest column
+ *            first, as Algorithm 3's kernel runs from r.x - r.z up to r.x in the
+ *            paper's frame.  Variants (Sec. Patcher: "height of h, h = 3 by
+ *            default"): kernel_rows = h gives rows v - (h-1)/2 .. v + (h-1)/2, and
+ *            nearest_first visits each row's columns from R up instead.
  *   A candidate is skipped if it is a hole (it carries no color) or if it is
  *   strictly nearer than d_occ (a foreground pixel, observation O2).  Otherwise:
  *       wgt   = wrem / 2 + 0.3 wrem t   (Eq. 6, evaluated as (wrem * 0.5) +
@@ -190,7 +195,7 @@ void oracle_hole_edges(int w, int h, const int32_t* src, int32_t* L, int32_t* R)
  *   warped color at (v, R) if R < w_img, else at (v, L) if L >= 0, else zero.
  */
 static void fill_one(int w, int h, int v, int u, int L, int R, const int32_t* src, const float* zt,
-                     const uint8_t* warped, uint8_t out[4])
+                     const uint8_t* warped, int kernel_rows, int nearest_first, uint8_t out[4])
 {
     if (R < w) {
         int wd = R - L;
@@ -198,11 +203,13 @@ static void fill_one(int w, int h, int v, int u, int L, int R, const int32_t* sr
         float t = (float)(R - u) / (float)wd;
         float acc[4] = { 0.0f, 0.0f, 0.0f, 0.0f };
         float wrem = 1.0f;
-        for (int vv = v - 1; vv <= v + 1; ++vv) {
+        int hr = (kernel_rows - 1) / 2;
+        int jhi = R + wd;
+        if (jhi > w - 1) jhi = w - 1;
+        for (int vv = v - hr; vv <= v + hr; ++vv) {
             if (vv < 0 || vv >= h) continue;
-            int jhi = R + wd;
-            if (jhi > w - 1) jhi = w - 1;
-            for (int j = jhi; j >= R; --j) {
+            for (int s = 0; s <= jhi - R; ++s) {
+                int j = nearest_first ? R + s : jhi - s;
                 size_t q = (size_t)vv * (size_t)w + (size_t)j;
                 if (src[q] < 0) continue;
                 if (zt[q] < d_occ) continue;
@@ -238,9 +245,13 @@ static void fill_one(int w, int h, int v, int u, int L, int R, const int32_t* sr
 /*
  * Fill every hole pixel (mask = 1) of `warped` (the resolved image) into out_color;
  * reached pixels are copied unchanged.  Candidates are read from `warped` only.
+ * kernel_rows is the kernel height h of the Patcher (odd, >= 1; the paper's default
+ * is 3): rows v - (h-1)/2 .. v + (h-1)/2.  nearest_first = 0 visits each row's columns
+ * from the farthest, min(R + w, W - 1), down to R (the paper's order, mirrored);
+ * nearest_first = 1 visits them from R up.
  */
-void oracle_fill(int w, int h, const int32_t* src, const float* zt, const int32_t* L, const int32_t* R,
-                 const uint8_t* warped, uint8_t* out_color)
+void oracle_fill_ex(int w, int h, const int32_t* src, const float* zt, const int32_t* L, const int32_t* R,
+                    const uint8_t* warped, int kernel_rows, int nearest_first, uint8_t* out_color)
 {
     for (int v = 0; v < h; ++v) {
         for (int u = 0; u < w; ++u) {
@@ -249,9 +260,15 @@ void oracle_fill(int w, int h, const int32_t* src, const float* zt, const int32_
                 memcpy(out_color + 4 * i, warped + 4 * i, 4);
                 continue;
             }
-            fill_one(w, h, v, u, L[i], R[i], src, zt, warped, out_color + 4 * i);
+            fill_one(w, h, v, u, L[i], R[i], src, zt, warped, kernel_rows, nearest_first, out_color + 4 * i);
         }
     }
+}
+
+void oracle_fill(int w, int h, const int32_t* src, const float* zt, const int32_t* L, const int32_t* R,
+                 const uint8_t* warped, uint8_t* out_color)
+{
+    oracle_fill_ex(w, h, src, zt, L, R, warped, 3, 0, out_color);
 }
 
 /*
@@ -260,14 +277,14 @@ void oracle_fill(int w, int h, const int32_t* src, const float* zt, const int32_
  * shared intrinsics the vertical coordinate is unchanged and cx cancels.
  * Returns 0, -1 on bad sizes, -2 if a temporary could not be allocated.
  */
-int oracle_synthesize(int w, int h, float fx, float fy, float cx, float cy, float ipd, float near_,
-                      float far_, const uint8_t* color, const float* depth, uint8_t* out_color,
-                      uint8_t* mask)
+int oracle_synthesize_ex(int w, int h, float fx, float fy, float cx, float cy, float ipd, float near_,
+                         float far_, const uint8_t* color, const float* depth, int kernel_rows, int nearest_first,
+                         uint8_t* out_color, uint8_t* mask)
 {
     (void)fy;
     (void)cx;
     (void)cy;
-    if (w < 0 || h < 0) return -1;
+    if (w < 0 || h < 0 || kernel_rows < 1 || (kernel_rows & 1) == 0) return -1;
     size_t n = (size_t)w * (size_t)h;
     if (n == 0) return 0;
     int32_t* xt = (int32_t*)malloc(n * sizeof(int32_t));
@@ -285,7 +302,7 @@ int oracle_synthesize(int w, int h, float fx, float fy, float cx, float cy, floa
         oracle_forward_warp(w, h, xt, zc, src, zt);
         oracle_resolve(w, h, color, src, warped, mask);
         oracle_hole_edges(w, h, src, L, R);
-        oracle_fill(w, h, src, zt, L, R, warped, out_color);
+        oracle_fill_ex(w, h, src, zt, L, R, warped, kernel_rows, nearest_first, out_color);
     }
     free(xt);
     free(zc);
@@ -295,4 +312,11 @@ int oracle_synthesize(int w, int h, float fx, float fy, float cx, float cy, floa
     free(R);
     free(warped);
     return rc;
+}
+
+int oracle_synthesize(int w, int h, float fx, float fy, float cx, float cy, float ipd, float near_,
+                      float far_, const uint8_t* color, const float* depth, uint8_t* out_color,
+                      uint8_t* mask)
+{
+    return oracle_synthesize_ex(w, h, fx, fy, cx, cy, ipd, near_, far_, color, depth, 3, 0, out_color, mask);
 }

@@ -30,9 +30,11 @@ MUTANTS = {
     "no_depth_gate": ("if (zt[q] < d_occ) continue;", ""),
     "gate_on_background_edge": ("float d_occ = (L >= 0) ? zt[(size_t)v * (size_t)w + (size_t)L] : 0.0f;",
                                 "float d_occ = zt[(size_t)v * (size_t)w + (size_t)R];"),
-    "nearest_column_first": ("for (int j = jhi; j >= R; --j) {", "for (int j = R; j <= jhi; ++j) {"),
+    "column_order_swapped": ("int j = nearest_first ? R + s : jhi - s;", "int j = nearest_first ? jhi - s : R + s;"),
+    "column_order_flag_ignored": ("int j = nearest_first ? R + s : jhi - s;", "int j = jhi - s;"),
     "kernel_one_column_short": ("int jhi = R + wd;", "int jhi = R + wd - 1;"),
-    "single_row_kernel": ("for (int vv = v - 1; vv <= v + 1; ++vv) {", "for (int vv = v; vv <= v; ++vv) {"),
+    "single_row_kernel": ("for (int vv = v - hr; vv <= v + hr; ++vv) {", "for (int vv = v; vv <= v; ++vv) {"),
+    "kernel_height_ignored": ("int hr = (kernel_rows - 1) / 2;", "int hr = 1;"),
     "divide_by_wrem": ("float den = 1.0f - wrem;", "float den = wrem;"),
     "fallback_to_occluder": ("    if (R < w)\n        memcpy(out, warped + 4 * ((size_t)v * (size_t)w + (size_t)R), 4);",
                              "    if (L >= 0)\n        memcpy(out, warped + 4 * ((size_t)v * (size_t)w + (size_t)L), 4);"),

@@ -211,11 +211,11 @@ def test_hole_edges_brute_force(seed):
 
 
 # ----------------------------------------------------------------------------- fill
-def _fill_case(valid, zt, colors):
+def _fill_case(valid, zt, colors, kernel_rows=3, nearest_first=False):
     src = np.where(valid, 0, -1).astype(np.int32)
     L, R = oracle.hole_edges(src)
     warped = np.where(valid[..., None], colors, 0).astype(np.uint8)
-    return oracle.fill(src, zt.astype(np.float32), L, R, warped), L, R
+    return oracle.fill(src, zt.astype(np.float32), L, R, warped, kernel_rows, nearest_first), L, R
 
 
 def test_fill_golden_two_contributors():
@@ -238,7 +238,7 @@ def test_fill_golden_two_contributors():
     assert out[0, 4].tolist() == by_t[Fraction(1, 3)]["expected"]
 
 
-def _expected_fill(valid, zt, colors, v, u):
+def _expected_fill(valid, zt, colors, v, u, kernel_rows=3, nearest_first=False):
     """Closed form of Algorithm 3 + Eq. 6 (exact rationals) for hole pixel (v, u).
 
     With q = 1/2 - 3t/10, the i-th contributor (0-based, in kernel order) receives
@@ -263,10 +263,12 @@ def _expected_fill(valid, zt, colors, v, u):
     t = Fraction(R - u, wd)
     q = Fraction(1, 2) - Fraction(3, 10) * t
     contrib = []
-    for vv in (v - 1, v, v + 1):
+    hr = (kernel_rows - 1) // 2
+    for vv in range(v - hr, v + hr + 1):
         if not 0 <= vv < h:
             continue
-        for j in range(min(R + wd, w - 1), R - 1, -1):
+        cols = range(min(R + wd, w - 1), R - 1, -1)
+        for j in (reversed(cols) if nearest_first else cols):
             if valid[vv, j] and not zt[vv, j] < d_occ:
                 contrib.append(colors[vv, j])
     if not contrib:
@@ -309,6 +311,98 @@ def test_fill_matches_geometric_closed_form(seed):
                 assert out[v, u, ch] == int(e + Fraction(1, 2)), (v, u, ch, float(e))
                 checked += 1
     assert checked > 50
+
+
+@pytest.mark.parametrize("kernel_rows,nearest_first", [(1, False), (1, True), (3, True), (5, False), (5, True),
+                                                      (7, False)])
+def test_fill_variants_match_geometric_closed_form(kernel_rows, nearest_first):
+    """The Patcher's variants (kernel height h, nearest-first column order): every hole
+    pixel equals the closed form sum q^i c_i / sum q^i over its kernel (or the fallback)."""
+    rng = np.random.default_rng(2000 + kernel_rows * 2 + int(nearest_first))
+    h, w = 9, 30
+    valid = rng.random((h, w)) < 0.6
+    zt = rng.choice(np.array([1.0, 2.0, 5.0, 5.0, 9.0]), (h, w)).astype(np.float32)
+    zt = np.where(valid, zt, np.inf).astype(np.float32)
+    colors = rng.integers(0, 256, (h, w, 4), dtype=np.uint8)
+    out, _, _ = _fill_case(valid, zt, colors, kernel_rows, nearest_first)
+    checked = 0
+    for v in range(h):
+        for u in range(w):
+            if valid[v, u]:
+                continue
+            exact, fb = _expected_fill(valid, zt, colors, v, u, kernel_rows, nearest_first)
+            if exact is None:
+                assert out[v, u].tolist() == fb.tolist()
+                continue
+            for ch in range(4):
+                e = exact[ch]
+                if abs(e - int(e) - Fraction(1, 2)) < Fraction(1, 100):
+                    continue  # too close to a rounding tie for binary32 to decide like exact math
+                assert out[v, u, ch] == int(e + Fraction(1, 2)), (v, u, ch, float(e))
+                checked += 1
+    assert checked > 100
+
+
+def test_fill_kernel_height_selects_the_rows():
+    """h = 1 reads row v only; h = 5 reaches rows v - 2 and v + 2, which h = 3 does not."""
+    h, w = 7, 20
+    v, L, R = 3, 4, 7  # hole at 5, 6 of row 3; kernel columns 10..7
+    valid = np.zeros((h, w), bool)
+    valid[:, : L + 1] = True
+    valid[v, R] = True           # the only contributor of row v
+    valid[v - 1, 8] = True       # rows v -+ 1: reached by h >= 3
+    valid[v + 2, 9] = True       # row v + 2: reached by h >= 5 only
+    zt = np.where(valid, 4.0, np.inf).astype(np.float32)
+    colors = np.zeros((h, w, 4), np.uint8)
+    colors[v, R] = (10, 20, 30, 255)
+    colors[v - 1, 8] = (200, 0, 0, 255)
+    colors[v + 2, 9] = (0, 0, 250, 255)
+    out1, _, _ = _fill_case(valid, zt, colors, kernel_rows=1)
+    assert out1[v, 5].tolist() == [10, 20, 30, 255]  # one contributor returns its color
+    out3, _, _ = _fill_case(valid, zt, colors, kernel_rows=3)
+    out5, _, _ = _fill_case(valid, zt, colors, kernel_rows=5)
+    assert out3[v, 5].tolist() != out1[v, 5].tolist()
+    assert out5[v, 5].tolist() != out3[v, 5].tolist()
+    # rows v-1..v+1 hold no contributor (R itself is nearer than the occluder): h = 3 falls
+    # back to the color at (v, R), h = 5 returns row v+2's color alone
+    valid2 = np.zeros((h, w), bool)
+    valid2[:, : L + 1] = True
+    valid2[v, R] = True
+    valid2[v + 2, 9] = True
+    zt2 = np.full((h, w), 5.0, np.float32)
+    zt2[v, R] = 1.0   # foreground: skipped by the depth gate
+    zt2[v + 2, 9] = 8.0
+    zt2 = np.where(valid2, zt2, np.inf).astype(np.float32)
+    colors2 = np.zeros((h, w, 4), np.uint8)
+    colors2[v, R] = (9, 9, 9, 255)
+    colors2[v + 2, 9] = (0, 0, 250, 255)
+    out_a, _, _ = _fill_case(valid2, zt2, colors2, kernel_rows=3)
+    out_b, _, _ = _fill_case(valid2, zt2, colors2, kernel_rows=5)
+    assert out_a[v, 5].tolist() == [9, 9, 9, 255]
+    assert out_b[v, 5].tolist() == [0, 0, 250, 255]
+
+
+def test_fill_column_order_changes_the_first_weight():
+    """Two contributors a (at R) and b (at R + 1) in a one-row kernel: the first one visited
+    gets weight 1 - q, the second q (1 - q), so the result is (c0 + q c1) / (1 + q) with c0
+    the first: b for the paper's farthest-first order, a for nearest-first."""
+    w = 12
+    L, R = 2, 5  # holes at 3, 4; w = 3, kernel columns 8..5
+    valid = np.zeros((1, w), bool)
+    valid[0, : L + 1] = True
+    valid[0, R] = valid[0, R + 1] = True
+    zt = np.where(valid, 4.0, np.inf).astype(np.float32)
+    colors = np.zeros((1, w, 4), np.uint8)
+    a, b = np.array([200, 10, 90, 255]), np.array([20, 230, 60, 255])
+    colors[0, R], colors[0, R + 1] = a, b
+    for nearest_first, first, second in ((False, b, a), (True, a, b)):
+        out, _, _ = _fill_case(valid, zt, colors, kernel_rows=1, nearest_first=nearest_first)
+        for u in (3, 4):
+            t = Fraction(R - u, R - L)
+            q = Fraction(1, 2) - Fraction(3, 10) * t
+            for ch in range(4):
+                e = (int(first[ch]) + q * int(second[ch])) / (1 + q)
+                assert out[0, u, ch] == int(e + Fraction(1, 2)), (nearest_first, u, ch)
 
 
 @pytest.mark.parametrize("t_num,t_den", [(1, 2), (1, 7), (6, 7), (4, 5)])
