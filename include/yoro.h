@@ -67,6 +67,15 @@ typedef struct {
     unsigned char* out_hole_mask;/* h*w bytes                            */
 } yoro_frame;
 
+/* Variants of the Patcher's kernel (Sec. Patcher).  yoro_create() takes the paper's
+ * kernel: height 3, columns visited farthest first. */
+typedef struct {
+    int kernel_rows;   /* kernel height h: odd, 1..15; rows v-(h-1)/2 .. v+(h-1)/2 (paper: 3) */
+    int nearest_first; /* 0: each row's columns from min(R + w, W - 1) down to R, the farthest
+                          first (the paper's order, mirrored to a left-eye source);
+                          1: from R up, the nearest first */
+} yoro_options;
+
 /*
  * Create a synthesis context for w x h frames of a stereo camera.
  *   fx, fy, cx, cy: pinhole intrinsics in pixels (shared by both eyes).  Only fx
@@ -82,7 +91,17 @@ typedef struct {
 yoro_handle yoro_create(int w, int h, float fx, float fy, float cx, float cy, float ipd,
                         float near_, float far_);
 
-/* Status of the last yoro_create() on the calling thread (YORO_OK after a success). */
+/* yoro_create() with a Patcher kernel variant (opt may be NULL: the paper's kernel).  The
+ * handle's synthesize calls (fused, unfused and host) use it; a frame whose band of one
+ * row with its kernel rows does not fit shared memory takes the global z-buffer path.
+ * Batch and no-alloc calls always use the paper's kernel.  Returns NULL with
+ * YORO_EINVAL for an even or out-of-range kernel_rows or a nearest_first other than
+ * 0 or 1. */
+yoro_handle yoro_create_ex(int w, int h, float fx, float fy, float cx, float cy, float ipd, float near_,
+                           float far_, const yoro_options* opt);
+
+/* Status of the last yoro_create() / yoro_create_ex() on the calling thread (YORO_OK
+ * after a success). */
 yoro_status yoro_last_create_error(void);
 
 /* Release the handle and the device memory it owns.  NULL is accepted.  Pending work

@@ -18,7 +18,7 @@ __all__ = [
     "yoro_synthesize_unfused", "yoro_synthesize_host", "yoro_synthesize_batch", "yoro_stream_status",
     "yoro_max_fused_width", "yoro_status_string", "yoro_last_create_error", "STATUS",
     "yoro_synthesize_noalloc", "yoro_noalloc_max_pixels", "yoro_tune_batch", "yoro_batch_band",
-    "yoro_reset_tuning",
+    "yoro_reset_tuning", "yoro_create_ex",
 ]
 
 _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "libyoro.so")
@@ -32,6 +32,10 @@ class YoroError(RuntimeError):
     def __init__(self, code: int, where: str):
         self.code = code
         super().__init__(f"{where}: {STATUS.get(code, code)} ({_status_string(code)})")
+
+
+class _Options(ctypes.Structure):
+    _fields_ = [("kernel_rows", ctypes.c_int), ("nearest_first", ctypes.c_int)]
 
 
 class _Frame(ctypes.Structure):
@@ -55,6 +59,8 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     P, I, F = ctypes.c_void_p, ctypes.c_int, ctypes.c_float
     lib.yoro_create.argtypes = [I, I, F, F, F, F, F, F, F]
     lib.yoro_create.restype = P
+    lib.yoro_create_ex.argtypes = [I, I, F, F, F, F, F, F, F, ctypes.POINTER(_Options)]
+    lib.yoro_create_ex.restype = P
     lib.yoro_last_create_error.argtypes = []
     lib.yoro_last_create_error.restype = I
     lib.yoro_destroy.argtypes = [P]
@@ -140,6 +146,16 @@ def yoro_create(w, h, fx, fy, cx, cy, ipd, near, far) -> _Handle:
     p = lib.yoro_create(int(w), int(h), fx, fy, cx, cy, ipd, near, far)
     if not p:
         raise YoroError(lib.yoro_last_create_error(), "yoro_create")
+    return _Handle(p, int(w), int(h))
+
+
+def yoro_create_ex(w, h, fx, fy, cx, cy, ipd, near, far, kernel_rows=3, nearest_first=False) -> _Handle:
+    """yoro_create with a Patcher kernel variant (height kernel_rows, nearest-first order)."""
+    lib = load_library()
+    opt = _Options(int(kernel_rows), int(bool(nearest_first)))
+    p = lib.yoro_create_ex(int(w), int(h), fx, fy, cx, cy, ipd, near, far, ctypes.byref(opt))
+    if not p:
+        raise YoroError(lib.yoro_last_create_error(), "yoro_create_ex")
     return _Handle(p, int(w), int(h))
 
 
@@ -241,9 +257,12 @@ def yoro_status_string(code: int) -> str:
 class Synthesizer:
     """Owns a handle for one camera; ``__call__`` allocates the outputs with torch."""
 
-    def __init__(self, w, h, fx, fy, cx, cy, ipd, near=0.05, far=1000.0):
+    def __init__(self, w, h, fx, fy, cx, cy, ipd, near=0.05, far=1000.0, kernel_rows=3, nearest_first=False):
         self.w, self.h = int(w), int(h)
-        self.handle = yoro_create(w, h, fx, fy, cx, cy, ipd, near, far)
+        if kernel_rows == 3 and not nearest_first:
+            self.handle = yoro_create(w, h, fx, fy, cx, cy, ipd, near, far)
+        else:
+            self.handle = yoro_create_ex(w, h, fx, fy, cx, cy, ipd, near, far, kernel_rows, nearest_first)
 
     def __call__(self, color: torch.Tensor, depth: torch.Tensor, stream=None, unfused: bool = False):
         out = torch.empty((self.h, self.w, 4), dtype=torch.uint8, device=color.device)

@@ -23,6 +23,8 @@ struct yoro_ctx {
     float fx, fy, cx, cy, ipd, near_, far_;
     float k;
     int device;
+    int halo, nearest;  // Patcher kernel shape (yoro_options)
+    bool fused_ok;      // the window of one band row fits shared memory
     FusedLimits lim;
     yoro::FusedShape shape;
     unsigned long long* d_zbuf;    // unfused path, h*w keys, allocated on first use
@@ -81,7 +83,16 @@ yoro_status make_frame(int w, int h, float k, float near_, float far_, const voi
     f->half_m = M < 0.5 ? (float)(0.5 - M) : 0.0f;  // rounding of 0.5 - M: below 2^-25, inside the slack
     f->band = 1;
     f->bulk = (w % 4 == 0) && aligned(color, 16) && aligned(depth, 16) && aligned(out, 16) && aligned(mask, 4);
+    f->halo = 1;  // the paper's kernel (h = 3, farthest column first) unless a handle says otherwise
+    f->nearest = 0;
     return YORO_OK;
+}
+
+// The handle's Patcher kernel shape on a frame description.
+void apply_options(const yoro_ctx* c, FrameArgs* f)
+{
+    f->halo = c->halo;
+    f->nearest = c->nearest;
 }
 
 yoro_status on_device(const yoro_ctx* c)
@@ -105,7 +116,7 @@ yoro_status run_unfused(yoro_ctx* c, const FrameArgs& f, cudaStream_t s)
 
 yoro_status run_frame(yoro_ctx* c, FrameArgs f, cudaStream_t s)
 {
-    if (f.w > c->lim.max_width) return run_unfused(c, f, s);
+    if (!c->fused_ok) return run_unfused(c, f, s);
     f.band = c->shape.band;
     return yoro::fused_launch(f, c->lim, c->shape.two_per_sm, s) == cudaSuccess ? YORO_OK : YORO_ECUDA;
 }
@@ -116,7 +127,16 @@ extern "C" {
 
 yoro_handle yoro_create(int w, int h, float fx, float fy, float cx, float cy, float ipd, float near_, float far_)
 {
-    if (!camera_ok(w, h, fx, fy, cx, cy, ipd, near_, far_)) {
+    return yoro_create_ex(w, h, fx, fy, cx, cy, ipd, near_, far_, nullptr);
+}
+
+yoro_handle yoro_create_ex(int w, int h, float fx, float fy, float cx, float cy, float ipd, float near_,
+                           float far_, const yoro_options* opt)
+{
+    const int kernel_rows = opt ? opt->kernel_rows : 3;
+    const int nearest = opt ? opt->nearest_first : 0;
+    if (!camera_ok(w, h, fx, fy, cx, cy, ipd, near_, far_) || kernel_rows < 1 || kernel_rows > 15 ||
+        (kernel_rows & 1) == 0 || (nearest != 0 && nearest != 1)) {
         g_last_create = YORO_EINVAL;
         return nullptr;
     }
@@ -141,7 +161,11 @@ yoro_handle yoro_create(int w, int h, float fx, float fy, float cx, float cy, fl
         g_last_create = YORO_ECUDA;
         return nullptr;
     }
-    c->shape = yoro::fused_shape(c->lim, w, h);
+    c->halo = (kernel_rows - 1) / 2;
+    c->nearest = nearest;
+    c->fused_ok = w <= c->lim.max_width &&
+                  yoro::fused_smem_bytes(yoro::fused_wpad(w), 1, c->halo) <= (size_t)c->lim.smem_per_block;
+    c->shape = yoro::fused_shape(c->lim, w, h, c->halo);
     g_last_create = YORO_OK;
     return c;
 }
@@ -166,6 +190,7 @@ yoro_status yoro_synthesize(yoro_handle c, const void* color, const float* depth
     FrameArgs f;
     st = make_frame(c->w, c->h, c->k, c->near_, c->far_, color, depth, out_color, out_mask, &f);
     if (st != YORO_OK) return st;
+    apply_options(c, &f);
     return run_frame(c, f, (cudaStream_t)stream);
 }
 
@@ -179,6 +204,7 @@ yoro_status yoro_synthesize_unfused(yoro_handle c, const void* color, const floa
     FrameArgs f;
     st = make_frame(c->w, c->h, c->k, c->near_, c->far_, color, depth, out_color, out_mask, &f);
     if (st != YORO_OK) return st;
+    apply_options(c, &f);
     return run_unfused(c, f, (cudaStream_t)stream);
 }
 
@@ -210,6 +236,7 @@ yoro_status yoro_synthesize_host(yoro_handle c, const void* hcolor, const float*
     FrameArgs f;
     st = make_frame(c->w, c->h, c->k, c->near_, c->far_, dc, dd, dout, dmask, &f);
     if (st != YORO_OK) return st;
+    apply_options(c, &f);
     st = run_frame(c, f, s);
     if (st != YORO_OK) return st;
     if (cudaMemcpyAsync(hout, dout, 4 * n, cudaMemcpyDeviceToHost, s) != cudaSuccess ||

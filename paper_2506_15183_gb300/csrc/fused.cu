@@ -60,6 +60,21 @@ struct Window {
     __device__ __forceinline__ const uint32_t* brow(int v) const { return bits + (v - ra) * nwords; }
 };
 
+// The Patcher's kernel shape (Sec. Patcher): rows v - halo .. v + halo (the kernel
+// height h = 2 halo + 1, the paper's default 3) and the column order in each row:
+// farthest first, min(R + w, W - 1) down to R (the paper's order, mirrored), or nearest
+// first, R up.  VAR = false compiles the paper's defaults as constants; VAR = true
+// takes them from the frame (the variant launch).
+template <bool VAR>
+struct KernelShape {
+    int halo;
+    bool nearest;
+    __device__ __forceinline__ explicit KernelShape(const FrameArgs& f)
+        : halo(VAR ? f.halo : 1), nearest(VAR ? f.nearest != 0 : false)
+    {
+    }
+};
+
 // Hole edges of pixel (v, x): L = highest reached column < x (or -1), R = lowest
 // reached column > x (or w), from the row's reached bitmask.
 __device__ __forceinline__ void find_edges(int x, int v, const Window& s, int w, int& L, int& R)
@@ -94,7 +109,9 @@ __device__ __forceinline__ void find_edges(int x, int v, const Window& s, int w,
 }
 
 // Hole fill of pixel (v, x) with edges L, R (R < w).  Rows outside [0, h) are skipped.
-__device__ __forceinline__ uint32_t fill_from_edges(int x, int v, int L, int R, int h, int w, const Window& s)
+template <bool VAR>
+__device__ __forceinline__ uint32_t fill_from_edges(int x, int v, int L, int R, int h, int w, const Window& s,
+                                                    const KernelShape<VAR>& ks)
 {
     const int wd = R - L;
     const float d_occ = (L >= 0) ? __uint_as_float(s.zrow(v)[L]) : 0.0f;
@@ -105,18 +122,19 @@ __device__ __forceinline__ uint32_t fill_from_edges(int x, int v, int L, int R, 
     const uint32_t mhi = ((jhi & 31) == 31) ? ~0u : ((2u << (jhi & 31)) - 1u);
     const uint32_t mlo = ~0u << (R & 31);
 #pragma unroll 1
-    for (int vv = v - 1; vv <= v + 1; ++vv) {
+    for (int vv = v - ks.halo; vv <= v + ks.halo; ++vv) {
         if (vv < 0 || vv >= h) continue;
         const uint32_t* b = s.brow(vv);
         const uint32_t* zr = s.zrow(vv);
         const uint32_t* cr = s.crow(vv);
 #pragma unroll 1
-        for (int wi = whi; wi >= wlo; --wi) {
+        for (int step = 0; step <= whi - wlo; ++step) {
+            const int wi = ks.nearest ? wlo + step : whi - step;
             uint32_t m = b[wi];
             if (wi == whi) m &= mhi;
             if (wi == wlo) m &= mlo;
             while (m) {
-                const int bit = 31 - __clz(m);
+                const int bit = ks.nearest ? __ffs(m) - 1 : 31 - __clz(m);
                 m &= ~(1u << bit);
                 const int c = (wi << 5) + bit;
                 if (__uint_as_float(zr[c]) < d_occ) continue;  // foreground (O2)
@@ -136,8 +154,9 @@ __device__ __forceinline__ uint32_t fill_from_edges(int x, int v, int L, int R, 
 // lanes; each lane accumulates it with its own t and stops at its own exact exit.  A
 // kernel full of foreground candidates is thus crossed 32 columns per step instead of
 // one candidate per step.
+template <bool VAR>
 __device__ __forceinline__ uint32_t fill_hole_warp(int x, bool act, int v, int L, int R, int h, int w,
-                                                   const Window& s)
+                                                   const Window& s, const KernelShape<VAR>& ks)
 {
     const int lane = threadIdx.x & 31;
     const int wd = R - L;
@@ -147,13 +166,14 @@ __device__ __forceinline__ uint32_t fill_hole_warp(int x, bool act, int v, int L
     bool done = !act;
     uint32_t res = 0u;
     const int jhi = min(R + wd, w - 1);
-    const int jlast = min(v + 1, h - 1) - s.ra;
-    for (int j = max(v - 1, 0) - s.ra; j <= jlast; ++j) {
-        for (int c0 = jhi; c0 >= R; c0 -= 32) {
-            const int c = c0 - lane;  // lane 0 takes the farthest column of the group
+    const int jlast = min(v + ks.halo, h - 1) - s.ra;
+    for (int j = max(v - ks.halo, 0) - s.ra; j <= jlast; ++j) {
+        for (int g0 = 0; g0 <= jhi - R; g0 += 32) {
+            // lane 0 takes the group's first column in kernel order
+            const int c = ks.nearest ? R + g0 + lane : jhi - g0 - lane;
             bool contrib = false;
             uint32_t col = 0u;
-            if (c >= R) {
+            if (ks.nearest ? c <= jhi : c >= R) {
                 const int i = j * s.wpad + c;
                 const bool reached = (s.bits[j * s.nwords + (c >> 5)] >> (c & 31)) & 1u;
                 contrib = reached && !(__uint_as_float(s.zt[i]) < d_occ);  // not foreground (O2)
@@ -185,19 +205,22 @@ __device__ __forceinline__ uint32_t fill_hole_warp(int x, bool act, int v, int L
 }
 
 // Hole fill of a one-pixel crack (v, x): reached pixels at x-1 and x+1, so L = x-1,
-// R = x+1, w = 2 and t = 1/2.  The kernel is rows v-1, v, v+1 times columns
-// min(x+3, W-1) .. x+1; all nine slots are visited in the same order as fill_from_edges,
+// R = x+1, w = 2 and t = 1/2.  The kernel is rows v-1, v, v+1 (v - halo .. v + halo)
+// times columns min(x+3, W-1) .. x+1 (or x+1 .. x+3 nearest first); all slots are
+// visited in the same order as fill_from_edges,
 // without early exits.  A slot that does not contribute (outside the image, a hole, or
 // nearer than the occluder) is given weight 0, which leaves acc and wrem unchanged
 // exactly, so the result equals the general loop's.
-__device__ __forceinline__ uint32_t fill_crack(int x, int v, int h, int w, const Window& s)
+template <bool VAR>
+__device__ __forceinline__ uint32_t fill_crack(int x, int v, int h, int w, const Window& s,
+                                               const KernelShape<VAR>& ks)
 {
     const float d_occ = __uint_as_float(s.zrow(v)[x - 1]);
     FillAcc f;
     f.init(0.5f);
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        const int vv = v - 1 + k;
+    for (int k = 0; k <= 2 * ks.halo; ++k) {
+        const int vv = v - ks.halo + k;
         const bool row_in = vv >= 0 && vv < h;
         const int vr = row_in ? vv : v;  // a valid row to read when vv is outside
         const uint32_t* b = s.brow(vr);
@@ -205,7 +228,7 @@ __device__ __forceinline__ uint32_t fill_crack(int x, int v, int h, int w, const
         const uint32_t* cr = s.crow(vr);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            const int col = x + 3 - c;
+            const int col = ks.nearest ? x + 1 + c : x + 3 - c;
             const bool col_in = col < w;
             const int cc = col_in ? col : x + 1;
             const bool reached = (b[cc >> 5] >> (cc & 31)) & 1u;
@@ -399,14 +422,15 @@ __device__ __forceinline__ void resolve_window(const FrameArgs& f, const float* 
 // One band [y0, y1) of one frame; shared memory holds the window rows ra..rb
 // (ra = y0-1 or 0, rb = y1 or h-1).  Ends with a barrier, so the next band may reuse
 // shared memory.
-template <int NT>
+template <int NT, bool VAR>
 __device__ __forceinline__ void run_band(const FrameArgs& f, int y0, int y1, Window s, int* ctr, int* rowinfo)
 {
     constexpr int NW = NT / 32;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int w = f.w, h = f.h;
     const int nwords = s.nwords;
-    const int ra = max(y0 - 1, 0), rb = min(y1, h - 1);
+    const KernelShape<VAR> ks(f);
+    const int ra = max(y0 - ks.halo, 0), rb = min(y1 - 1 + ks.halo, h - 1);
     const int nr = rb - ra + 1;
     s.ra = ra;
     const float* depth = f.depth + (size_t)ra * w;
@@ -554,11 +578,11 @@ __device__ __forceinline__ void run_band(const FrameArgs& f, int y0, int y1, Win
                 const int v0 = __shfl_sync(0xffffffffu, v, 0), L0 = __shfl_sync(0xffffffffu, L, 0),
                           R0 = __shfl_sync(0xffffffffu, R, 0);
                 if (__all_sync(0xffffffffu, !act || (v == v0 && L == L0 && R == R0)))
-                    o = fill_hole_warp(x, act, v0, L0, R0, h, w, s);
+                    o = fill_hole_warp<VAR>(x, act, v0, L0, R0, h, w, s, ks);
                 else if (act)
-                    o = fill_from_edges(x, v, L, R, h, w, s);
+                    o = fill_from_edges<VAR>(x, v, L, R, h, w, s, ks);
             } else if (act) {
-                o = fill_crack(x, v, h, w, s);
+                o = fill_crack<VAR>(x, v, h, w, s, ks);
             }
             if (act) f.out[(size_t)v * w + x] = o;
         }
@@ -584,16 +608,16 @@ __device__ __forceinline__ Window window_layout(unsigned char* smem, int slots, 
     return s;
 }
 
-template <int NT, int MINB>
+template <int NT, int MINB, bool VAR>
 __global__ void __launch_bounds__(NT, MINB) fused_single(FrameArgs f, int wpad)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     int *ctr, *rowinfo;
-    const Window s = window_layout(smem_raw, f.band + 2, wpad, f.w, ctr, rowinfo);
+    const Window s = window_layout(smem_raw, f.band + 2 * KernelShape<VAR>(f).halo, wpad, f.w, ctr, rowinfo);
     const int nbands = (f.h + f.band - 1) / f.band;
     for (int b = blockIdx.x; b < nbands; b += gridDim.x) {
         const int y0 = b * f.band;
-        run_band<NT>(f, y0, min(y0 + f.band, f.h), s, ctr, rowinfo);
+        run_band<NT, VAR>(f, y0, min(y0 + f.band, f.h), s, ctr, rowinfo);
     }
 }
 
@@ -612,7 +636,7 @@ __global__ void __launch_bounds__(NT, MINB) fused_batch(const __grid_constant__ 
         int *ctr, *rowinfo;
         const Window s = window_layout(smem_raw, a.max_band + 2, wpad, f.w, ctr, rowinfo);
         const int y0 = (item - a.item_start[lo]) * f.band;
-        run_band<NT>(f, y0, min(y0 + f.band, f.h), s, ctr, rowinfo);
+        run_band<NT, false>(f, y0, min(y0 + f.band, f.h), s, ctr, rowinfo);
     }
 }
 
@@ -625,9 +649,9 @@ constexpr int kSmall = 512;
 
 int fused_wpad(int w) { return ((w + 7) / 8) * 8; }
 
-size_t fused_smem_bytes(int wpad, int band)
+size_t fused_smem_bytes(int wpad, int band, int halo)
 {
-    const size_t slots = (size_t)band + 2;
+    const size_t slots = (size_t)band + 2 * (size_t)halo;
     // per pixel a source/depth word and a color word; per 32-pixel word a reached
     // bitmask and a hole prefix sum; two counters (16 bytes); per window row a last
     // reached column and a hole offset
@@ -647,10 +671,11 @@ cudaError_t fused_configure(int device, FusedLimits* lim)
     lim->smem_per_block = smem_optin;
     lim->smem_per_sm = smem_sm;
     int wmax = 0;  // widest frame with a band of one row
-    while (fused_smem_bytes(fused_wpad(wmax + 32), 1) <= (size_t)smem_optin && wmax + 32 <= 65535) wmax += 32;
+    while (fused_smem_bytes(fused_wpad(wmax + 32), 1, 1) <= (size_t)smem_optin && wmax + 32 <= 65535) wmax += 32;
     lim->max_width = wmax;
-    const void* fns[] = {(const void*)fused_single<kBig, 1>, (const void*)fused_single<kSmall, 2>,
-                         (const void*)fused_batch<kBig, 1>, (const void*)fused_batch<kSmall, 2>};
+    const void* fns[] = {(const void*)fused_single<kBig, 1, false>, (const void*)fused_single<kSmall, 2, false>,
+                         (const void*)fused_single<kBig, 1, true>,  (const void*)fused_single<kSmall, 2, true>,
+                         (const void*)fused_batch<kBig, 1>,         (const void*)fused_batch<kSmall, 2>};
     for (const void* fn : fns) {
         e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
         if (e != cudaSuccess) return e;
@@ -659,27 +684,27 @@ cudaError_t fused_configure(int device, FusedLimits* lim)
 }
 
 // Largest band whose rows fit the per-CTA shared memory.
-static int max_band(const FusedLimits& lim, int wpad)
+static int max_band(const FusedLimits& lim, int wpad, int halo)
 {
     if (wpad <= 0) return 1;
     int b = 1;
-    while (b < 4096 && fused_smem_bytes(wpad, b + 1) <= (size_t)lim.smem_per_block) ++b;
+    while (b < 4096 && fused_smem_bytes(wpad, b + 1, halo) <= (size_t)lim.smem_per_block) ++b;
     return b;
 }
 
 // Band height for a w x h frame: enough bands for every SM, each as tall as shared
 // memory allows up to that.  Two CTAs per SM when two such bands fit on an SM.
-FusedShape fused_shape(const FusedLimits& lim, int w, int h)
+FusedShape fused_shape(const FusedLimits& lim, int w, int h, int halo)
 {
     const int wpad = fused_wpad(w);
-    const int bmax = max_band(lim, wpad);
+    const int bmax = max_band(lim, wpad, halo);
     FusedShape s;
     int band = (h + lim.sms - 1) / lim.sms;
     if (band > bmax) band = bmax;
     if (band < 1) band = 1;
     // two CTAs of half the band height, if they fit beside each other
     const int half = (band + 1) / 2;
-    if (band >= 2 && 2 * (fused_smem_bytes(wpad, half) + 1024) <= (size_t)lim.smem_per_sm) {
+    if (band >= 2 && 2 * (fused_smem_bytes(wpad, half, halo) + 1024) <= (size_t)lim.smem_per_sm) {
         s.band = half;
         s.two_per_sm = 1;
     } else {
@@ -692,21 +717,25 @@ FusedShape fused_shape(const FusedLimits& lim, int w, int h)
 cudaError_t fused_launch(const FrameArgs& f, const FusedLimits& lim, int two_per_sm, cudaStream_t stream)
 {
     const int wpad = fused_wpad(f.w);
-    const size_t smem = fused_smem_bytes(wpad, f.band);
+    const size_t smem = fused_smem_bytes(wpad, f.band, f.halo);
+    const bool var = f.halo != 1 || f.nearest != 0;  // a Patcher variant: its own instantiation
     const int nbands = (f.h + f.band - 1) / f.band;
     const int slots = lim.sms * (two_per_sm ? 2 : 1);
     const int grid = nbands < slots ? nbands : slots;
-    if (two_per_sm)
-        fused_single<kSmall, 2><<<grid, kSmall, smem, stream>>>(f, wpad);
-    else
-        fused_single<kBig, 1><<<grid, kBig, smem, stream>>>(f, wpad);
+    if (two_per_sm) {
+        if (var) fused_single<kSmall, 2, true><<<grid, kSmall, smem, stream>>>(f, wpad);
+        else fused_single<kSmall, 2, false><<<grid, kSmall, smem, stream>>>(f, wpad);
+    } else {
+        if (var) fused_single<kBig, 1, true><<<grid, kBig, smem, stream>>>(f, wpad);
+        else fused_single<kBig, 1, false><<<grid, kBig, smem, stream>>>(f, wpad);
+    }
     return cudaGetLastError();
 }
 
 cudaError_t fused_launch_batch(const BatchArgs& a, int wmax, const FusedLimits& lim, cudaStream_t stream)
 {
     const int wpad = fused_wpad(wmax);
-    const size_t smem = fused_smem_bytes(wpad, a.max_band);
+    const size_t smem = fused_smem_bytes(wpad, a.max_band, 1);  // batch frames use the default kernel
     const bool two = 2 * (smem + 1024) <= (size_t)lim.smem_per_sm;
     // One CTA per (frame, band) item: the hardware block scheduler hands the next item to
     // whichever SM frees up first, so bands with heavy disocclusions do not hold back the
@@ -720,6 +749,6 @@ cudaError_t fused_launch_batch(const BatchArgs& a, int wmax, const FusedLimits& 
     return cudaGetLastError();
 }
 
-int fused_max_band(const FusedLimits& lim, int w) { return max_band(lim, fused_wpad(w)); }
+int fused_max_band(const FusedLimits& lim, int w, int halo) { return max_band(lim, fused_wpad(w), halo); }
 
 }  // namespace yoro

@@ -95,6 +95,8 @@ yoro_status yoro_synthesize_noalloc(int w, int h, float fx, float fy, float cx, 
     f.half_m = M < 0.5 ? (float)(0.5 - M) : 0.0f;
     f.band = 1;
     f.bulk = 0;
+    f.halo = 1;     // the paper's kernel: h = 3, farthest column first
+    f.nearest = 0;
     // unfused_launch clears the n keys it uses to the empty key before the scatter.
     return yoro::unfused_launch(f, zbuf, (cudaStream_t)stream) == cudaSuccess ? YORO_OK : YORO_ECUDA;
 }

@@ -66,10 +66,11 @@ __global__ void resolve_fill_kernel(FrameArgs f, const unsigned long long* __res
             acc.init(__fdiv_rn((float)(R - u), (float)wd));
             const int jhi = min(R + wd, w - 1);
             bool live = true, done = false;
-            for (int vv = v - 1; vv <= v + 1 && live; ++vv) {
+            for (int vv = v - f.halo; vv <= v + f.halo && live; ++vv) {
                 if (vv < 0 || vv >= f.h) continue;
                 const unsigned long long* zq = zbuf + (size_t)vv * w;
-                for (int j = jhi; j >= R; --j) {
+                for (int s = 0; s <= jhi - R; ++s) {
+                    const int j = f.nearest ? R + s : jhi - s;
                     const unsigned long long kq = zq[j];
                     if (kq == kEmptyKey) continue;
                     if (__uint_as_float((uint32_t)(kq >> 32)) < d_occ) continue;

@@ -20,6 +20,8 @@ struct FrameArgs {
     float half_m; // 0.5 - M: decision margin of the approximate disparity (host bound)
     int band;     // rows per CTA work item
     int bulk;     // 1: rows are 16-byte aligned (w % 4 == 0), bulk copies + vector stores
+    int halo;     // Patcher kernel rows on each side of v: kernel height 2 halo + 1 (default 1)
+    int nearest;  // 1: kernel columns nearest first (R up); 0: farthest first (default)
 };
 
 // Up to kMaxBatch frames travel in the kernel's parameter space (< 32 KB).
@@ -48,10 +50,10 @@ struct FusedShape {
 
 // fused.cu
 int fused_wpad(int w);
-size_t fused_smem_bytes(int wpad, int band);
+size_t fused_smem_bytes(int wpad, int band, int halo = 1);
 cudaError_t fused_configure(int device, FusedLimits* lim);
-FusedShape fused_shape(const FusedLimits& lim, int w, int h);
-int fused_max_band(const FusedLimits& lim, int w);
+FusedShape fused_shape(const FusedLimits& lim, int w, int h, int halo = 1);
+int fused_max_band(const FusedLimits& lim, int w, int halo = 1);
 cudaError_t fused_launch(const FrameArgs& f, const FusedLimits& lim, int two_per_sm, cudaStream_t stream);
 cudaError_t fused_launch_batch(const BatchArgs& a, int wmax, const FusedLimits& lim, cudaStream_t stream);
 

@@ -71,6 +71,15 @@ def test_create_rejects_bad_camera_without_touching_the_device(lib):
             yoro.yoro_create(*args)
 
 
+def test_create_ex_rejects_bad_options_without_touching_the_device(lib):
+    import paper_2506_15183_gb300 as yoro
+
+    for kr, nf in ((2, 0), (0, 0), (17, 0), (-1, 0), (3, 2)):
+        opt = yoro._Options(kr, nf)
+        assert lib.yoro_create_ex(64, 64, 32.0, 32.0, 32.0, 32.0, 0.06, 0.05, 1000.0, opt) is None
+        assert lib.yoro_last_create_error() == 1
+
+
 def test_null_handle_and_strings(lib):
     assert lib.yoro_synthesize(None, None, None, None, None, None) == 1
     assert lib.yoro_synthesize_unfused(None, None, None, None, None, None) == 1
