@@ -21,7 +21,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIBDIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(LIBDIR, "libyoro.so")
-SOURCES = ["api.cu", "fused.cu", "unfused.cu", "noalloc.cu"]
+SOURCES = ["api.cu", "fused.cu", "unfused.cu", "noalloc.cu", "server.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-fmad=false", "-Xcompiler", "-fPIC",
               "-Xptxas", "-v", f"-I{INCLUDE}", f"-I{CSRC}"]
@@ -35,7 +35,8 @@ def nvcc() -> str:
 
 
 def _inputs_mtime() -> float:
-    files = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(INCLUDE, "yoro.h"), __file__]
+    files = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE)]
+    files.append(__file__)
     return max(os.path.getmtime(f) for f in files if os.path.isfile(f))
 
 
@@ -62,7 +63,7 @@ def build_cuda(force: bool = False, verbose: bool = False) -> str:
     if verbose:
         print(log)
     tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *[o for o, _ in results]]
+    cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *[o for o, _ in results], "-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

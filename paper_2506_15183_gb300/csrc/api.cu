@@ -123,6 +123,14 @@ yoro_status run_frame(yoro_ctx* c, FrameArgs f, cudaStream_t s)
 
 }  // namespace
 
+namespace yoro {
+bool camera_valid(int w, int h, float fx, float fy, float cx, float cy, float ipd, float near_, float far_)
+{
+    return camera_ok(w, h, fx, fy, cx, cy, ipd, near_, far_);
+}
+void set_last_create_error(int st) { g_last_create = (yoro_status)st; }
+}  // namespace yoro
+
 extern "C" {
 
 yoro_handle yoro_create(int w, int h, float fx, float fy, float cx, float cy, float ipd, float near_, float far_)

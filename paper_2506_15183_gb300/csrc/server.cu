@@ -1,0 +1,365 @@
+// Serving loop: admitted streams with resident frame slots, continuous batching by a
+// scheduler thread.  Contract in include/yoro_server.h.
+//
+// The scheduler keeps up to two batches in flight on its own CUDA stream: it launches
+// whatever is pending as one yoro_synthesize_batch, and while that runs, gathers the
+// frames submitted meanwhile into the next launch; it then waits (a blocking-sync CUDA
+// event, so the thread sleeps) for the older batch and reports its frames complete.
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <condition_variable>
+#include <cstdint>
+#include <deque>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <vector>
+
+#include "yoro.h"
+#include "yoro_internal.h"
+#include "yoro_server.h"
+
+namespace {
+
+long long now_ns()
+{
+    return std::chrono::duration_cast<std::chrono::nanoseconds>(std::chrono::steady_clock::now().time_since_epoch())
+        .count();
+}
+
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+struct Slot {
+    void* color;
+    float* depth;
+    void* out;
+    unsigned char* mask;
+    bool in_flight;
+};
+
+struct Stream {
+    bool live = false;
+    int w = 0, h = 0;
+    float fx = 0, fy = 0, cx = 0, cy = 0, ipd = 0, near_ = 0, far_ = 0;
+    size_t bytes = 0;
+    unsigned char* block = nullptr;
+    std::vector<Slot> slots;
+    int pending = 0;  // submitted, not completed
+};
+
+struct Request {
+    int stream, slot;
+    unsigned long long tag;
+    long long submit_ns;
+};
+
+struct Batch {
+    std::vector<Request> req;
+    cudaEvent_t done = nullptr;
+    long long launch_ns = 0;
+    yoro_status status = YORO_OK;
+};
+
+constexpr int kMaxSlots = 64;
+constexpr int kInFlight = 2;
+
+}  // namespace
+
+struct yoro_server_ctx {
+    int device = 0;
+    size_t budget = 0, used = 0;
+    int max_batch = 0;
+    cudaStream_t cs = nullptr;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<Request> pending;
+    std::deque<yoro_completion> done;
+    std::vector<Stream> streams;
+    long long outstanding = 0;  // submitted and not completed
+    bool stop = false;
+    Batch ring[kInFlight];
+    std::thread worker;
+
+    void run();
+    void complete(Batch& b, long long t_done);
+};
+
+void yoro_server_ctx::complete(Batch& b, long long t_done)
+{
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        for (const Request& r : b.req) {
+            yoro_completion c;
+            c.stream = r.stream;
+            c.slot = r.slot;
+            c.tag = r.tag;
+            c.submit_ns = r.submit_ns;
+            c.launch_ns = b.launch_ns;
+            c.done_ns = t_done;
+            c.batch_frames = (int)b.req.size();
+            c.status = b.status;
+            done.push_back(c);
+            Stream& st = streams[r.stream];
+            st.slots[r.slot].in_flight = false;
+            --st.pending;
+            --outstanding;
+        }
+        b.req.clear();
+    }
+    cv_done.notify_all();
+}
+
+void yoro_server_ctx::run()
+{
+    cudaSetDevice(device);
+    std::vector<yoro_frame> frames;
+    int head = 0, count = 0;  // ring of batches in flight: oldest at head
+    for (;;) {
+        // Launch a new batch when one can be in flight and work is pending; otherwise
+        // wait for the oldest batch or for work.
+        bool launched = false;
+        if (count < kInFlight) {
+            Batch& b = ring[(head + count) % kInFlight];
+            {
+                std::unique_lock<std::mutex> lk(mu);
+                if (count == 0) cv_work.wait(lk, [&] { return stop || !pending.empty(); });
+                if (pending.empty() && count == 0 && stop) break;
+                frames.clear();
+                while (!pending.empty() && (int)b.req.size() < max_batch) {
+                    const Request r = pending.front();
+                    pending.pop_front();
+                    const Stream& st = streams[r.stream];
+                    const Slot& sl = st.slots[r.slot];
+                    yoro_frame f;
+                    f.w = st.w;
+                    f.h = st.h;
+                    f.fx = st.fx;
+                    f.fy = st.fy;
+                    f.cx = st.cx;
+                    f.cy = st.cy;
+                    f.ipd = st.ipd;
+                    f.near_ = st.near_;
+                    f.far_ = st.far_;
+                    f.color = sl.color;
+                    f.depth = sl.depth;
+                    f.out_color = sl.out;
+                    f.out_hole_mask = sl.mask;
+                    frames.push_back(f);
+                    b.req.push_back(r);
+                }
+            }
+            if (!b.req.empty()) {
+                b.launch_ns = now_ns();
+                b.status = yoro_synthesize_batch((int)frames.size(), frames.data(), cs);
+                if (b.status == YORO_OK && cudaEventRecord(b.done, cs) != cudaSuccess) b.status = YORO_ECUDA;
+                ++count;
+                launched = true;
+            }
+        }
+        if (count == 0) continue;
+        if (launched && count < kInFlight) continue;  // gather the next batch while this one runs
+        Batch& old = ring[head];
+        if (old.status == YORO_OK && cudaEventSynchronize(old.done) != cudaSuccess) old.status = YORO_ECUDA;
+        if (old.status != YORO_OK) cudaGetLastError();
+        complete(old, now_ns());
+        head = (head + 1) % kInFlight;
+        --count;
+    }
+}
+
+extern "C" {
+
+yoro_server yoro_server_create(size_t memory_budget_bytes, int max_batch)
+{
+    if (memory_budget_bytes == 0 || max_batch < 1 || max_batch > 4096) {
+        yoro::set_last_create_error(YORO_EINVAL);
+        return nullptr;
+    }
+    yoro_server_ctx* s = new (std::nothrow) yoro_server_ctx();
+    if (!s) {
+        yoro::set_last_create_error(YORO_ENOMEM);
+        return nullptr;
+    }
+    s->budget = memory_budget_bytes;
+    s->max_batch = max_batch;
+    bool ok = cudaGetDevice(&s->device) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&s->cs, cudaStreamNonBlocking) == cudaSuccess;
+    for (int i = 0; ok && i < kInFlight; ++i)
+        ok = cudaEventCreateWithFlags(&s->ring[i].done, cudaEventBlockingSync | cudaEventDisableTiming) ==
+             cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        for (Batch& b : s->ring)
+            if (b.done) cudaEventDestroy(b.done);
+        if (s->cs) cudaStreamDestroy(s->cs);
+        delete s;
+        yoro::set_last_create_error(YORO_ECUDA);
+        return nullptr;
+    }
+    try {
+        s->worker = std::thread([s] { s->run(); });
+    } catch (...) {
+        for (Batch& b : s->ring) cudaEventDestroy(b.done);
+        cudaStreamDestroy(s->cs);
+        delete s;
+        yoro::set_last_create_error(YORO_ENOMEM);
+        return nullptr;
+    }
+    yoro::set_last_create_error(YORO_OK);
+    return s;
+}
+
+void yoro_server_destroy(yoro_server s)
+{
+    if (!s) return;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stop = true;
+    }
+    s->cv_work.notify_all();
+    if (s->worker.joinable()) s->worker.join();
+    cudaStreamSynchronize(s->cs);
+    for (Stream& st : s->streams)
+        if (st.block) cudaFree(st.block);
+    for (Batch& b : s->ring) cudaEventDestroy(b.done);
+    cudaStreamDestroy(s->cs);
+    delete s;
+}
+
+int yoro_server_admit(yoro_server s, int w, int h, float fx, float fy, float cx, float cy, float ipd, float near_,
+                      float far_, int slots)
+{
+    if (!s || slots < 1 || slots > kMaxSlots || !yoro::camera_valid(w, h, fx, fy, cx, cy, ipd, near_, far_) ||
+        (size_t)w * (size_t)h == 0)
+        return -YORO_EINVAL;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != s->device) {
+        cudaGetLastError();
+        return -YORO_EINVAL;
+    }
+    if (w > yoro_max_fused_width()) return -YORO_ETOOBIG;
+    const size_t n = (size_t)w * (size_t)h;
+    const size_t per_slot = 3 * align256(4 * n) + align256(n);
+    const size_t bytes = per_slot * (size_t)slots;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (s->used + bytes > s->budget) return -YORO_ENOMEM;
+        s->used += bytes;  // reserved while the allocation runs
+    }
+    unsigned char* block = nullptr;
+    if (cudaMalloc(&block, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->used -= bytes;
+        return -YORO_ENOMEM;
+    }
+    Stream st;
+    st.live = true;
+    st.w = w;
+    st.h = h;
+    st.fx = fx;
+    st.fy = fy;
+    st.cx = cx;
+    st.cy = cy;
+    st.ipd = ipd;
+    st.near_ = near_;
+    st.far_ = far_;
+    st.bytes = bytes;
+    st.block = block;
+    for (int i = 0; i < slots; ++i) {
+        unsigned char* p = block + per_slot * (size_t)i;
+        Slot sl;
+        sl.color = p;
+        sl.depth = reinterpret_cast<float*>(p + align256(4 * n));
+        sl.out = p + 2 * align256(4 * n);
+        sl.mask = p + 3 * align256(4 * n);
+        sl.in_flight = false;
+        st.slots.push_back(sl);
+    }
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->streams.push_back(std::move(st));
+    return (int)s->streams.size() - 1;
+}
+
+yoro_status yoro_server_leave(yoro_server s, int stream)
+{
+    if (!s) return YORO_EINVAL;
+    unsigned char* block = nullptr;
+    {
+        std::unique_lock<std::mutex> lk(s->mu);
+        if (stream < 0 || stream >= (int)s->streams.size() || !s->streams[stream].live) return YORO_EINVAL;
+        s->cv_done.wait(lk, [&] { return s->streams[stream].pending == 0; });
+        Stream& st = s->streams[stream];
+        st.live = false;
+        block = st.block;
+        st.block = nullptr;
+        s->used -= st.bytes;
+        st.bytes = 0;
+        st.slots.clear();
+    }
+    return cudaFree(block) == cudaSuccess ? YORO_OK : YORO_ECUDA;
+}
+
+yoro_status yoro_server_slot(yoro_server s, int stream, int slot, void** color, float** depth, void** out_color,
+                             unsigned char** out_hole_mask)
+{
+    if (!s) return YORO_EINVAL;
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (stream < 0 || stream >= (int)s->streams.size() || !s->streams[stream].live) return YORO_EINVAL;
+    const Stream& st = s->streams[stream];
+    if (slot < 0 || slot >= (int)st.slots.size()) return YORO_EINVAL;
+    const Slot& sl = st.slots[slot];
+    if (color) *color = sl.color;
+    if (depth) *depth = sl.depth;
+    if (out_color) *out_color = sl.out;
+    if (out_hole_mask) *out_hole_mask = sl.mask;
+    return YORO_OK;
+}
+
+yoro_status yoro_server_submit(yoro_server s, int stream, int slot, unsigned long long tag)
+{
+    if (!s) return YORO_EINVAL;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (stream < 0 || stream >= (int)s->streams.size() || !s->streams[stream].live) return YORO_EINVAL;
+        Stream& st = s->streams[stream];
+        if (slot < 0 || slot >= (int)st.slots.size() || st.slots[slot].in_flight) return YORO_EINVAL;
+        st.slots[slot].in_flight = true;
+        ++st.pending;
+        ++s->outstanding;
+        s->pending.push_back(Request{stream, slot, tag, now_ns()});
+    }
+    s->cv_work.notify_one();
+    return YORO_OK;
+}
+
+int yoro_server_poll(yoro_server s, yoro_completion* out, int max)
+{
+    if (!s || !out || max <= 0) return 0;
+    std::lock_guard<std::mutex> lk(s->mu);
+    int n = 0;
+    while (n < max && !s->done.empty()) {
+        out[n++] = s->done.front();
+        s->done.pop_front();
+    }
+    return n;
+}
+
+yoro_status yoro_server_drain(yoro_server s, int timeout_ms)
+{
+    if (!s) return YORO_EINVAL;
+    std::unique_lock<std::mutex> lk(s->mu);
+    const bool ok = s->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms < 0 ? 0 : timeout_ms),
+                                        [&] { return s->outstanding == 0; });
+    return ok ? YORO_OK : YORO_ECUDA;
+}
+
+size_t yoro_server_memory_used(yoro_server s)
+{
+    if (!s) return 0;
+    std::lock_guard<std::mutex> lk(s->mu);
+    return s->used;
+}
+
+}  // extern "C"

@@ -57,6 +57,10 @@ int fused_max_band(const FusedLimits& lim, int w, int halo = 1);
 cudaError_t fused_launch(const FrameArgs& f, const FusedLimits& lim, int two_per_sm, cudaStream_t stream);
 cudaError_t fused_launch_batch(const BatchArgs& a, int wmax, const FusedLimits& lim, cudaStream_t stream);
 
+// api.cu: the camera checks of yoro_create, and the status yoro_last_create_error reports.
+bool camera_valid(int w, int h, float fx, float fy, float cx, float cy, float ipd, float near_, float far_);
+void set_last_create_error(int status);
+
 // unfused.cu: separate kernels around a global z-buffer of h*w keys.
 cudaError_t unfused_launch(const FrameArgs& f, unsigned long long* zbuf, cudaStream_t stream);
 

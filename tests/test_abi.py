@@ -80,6 +80,22 @@ def test_create_ex_rejects_bad_options_without_touching_the_device(lib):
         assert lib.yoro_last_create_error() == 1
 
 
+def test_server_rejects_bad_arguments_without_touching_the_device(lib):
+    from paper_2506_15183_gb300 import server
+
+    sl = server._lib()
+    assert sl.yoro_server_create(0, 8) is None and sl.yoro_last_create_error() == 1
+    assert sl.yoro_server_create(1 << 30, 0) is None and sl.yoro_last_create_error() == 1
+    assert sl.yoro_server_create(1 << 30, 5000) is None and sl.yoro_last_create_error() == 1
+    assert sl.yoro_server_admit(None, 64, 64, 32.0, 32.0, 32.0, 32.0, 0.06, 0.05, 1000.0, 2) == -1
+    assert sl.yoro_server_leave(None, 0) == 1
+    assert sl.yoro_server_submit(None, 0, 0, 0) == 1
+    assert sl.yoro_server_poll(None, None, 4) == 0
+    assert sl.yoro_server_drain(None, 10) == 1
+    assert sl.yoro_server_memory_used(None) == 0
+    sl.yoro_server_destroy(None)
+
+
 def test_null_handle_and_strings(lib):
     assert lib.yoro_synthesize(None, None, None, None, None, None) == 1
     assert lib.yoro_synthesize_unfused(None, None, None, None, None, None) == 1
