@@ -18,7 +18,6 @@ one host core) on the same workload; under torchrun only rank 0 runs it.
 from __future__ import annotations
 
 import argparse
-import glob
 import hashlib
 import json
 import re
@@ -94,13 +93,15 @@ def _code_only(src: str) -> str:
     return " ".join(src.split())
 
 
+KERNEL_SOURCES = ("fused.cu", "yoro_device.cuh", "yoro_internal.h")  # what the fused kernel is built from
+
+
 def csrc_digest() -> str:
-    """Digest of the kernel sources' code (comments and layout ignored), to tell whether
-    stored ncu counters still describe the kernel."""
+    """Digest of the fused kernel's sources (comments and layout ignored), to tell
+    whether stored ncu counters still describe the kernel."""
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(CSRC, "*"))):
-        if os.path.isfile(f) and f.endswith((".cu", ".cuh", ".h")):
-            h.update(_code_only(open(f, encoding="utf-8").read()).encode())
+    for name in KERNEL_SOURCES:
+        h.update(_code_only(open(os.path.join(CSRC, name), encoding="utf-8").read()).encode())
     return h.hexdigest()[:16]
 
 

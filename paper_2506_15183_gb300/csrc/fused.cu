@@ -1,10 +1,10 @@
 // Fused second-eye synthesis kernel for GB300 (sm_103a).
 //
 // One CTA synthesizes a band of B output rows at once; shared memory holds the
-// band's warped rows plus one halo row above and below (the window, rows
-// y0-1 .. y0+B): per target pixel a 32-bit word that is first the source column and
-// then the depth, a 32-bit RGBA8 word, and a reached bit.  Four steps, three CTA
-// barriers per band:
+// band's warped rows plus the kernel's halo rows above and below (the window; one halo
+// row per side for the paper's 3-row kernel): per target pixel a 32-bit word that is
+// first the source column and then the depth, a 32-bit RGBA8 word, a reached bit, and
+// per 32-pixel word a hole prefix sum.  The steps, separated by CTA barriers:
 //
 //   0.  one warp starts 1-D bulk prefetches of the window's depth and color rows
 //       into L2 (cp.async.bulk.prefetch.L2), while all threads clear the window;
@@ -17,11 +17,13 @@
 //   P2  resolve + gather: each reached target loads its source's depth and color;
 //       warp ballots write the rows' reached-pixel bitmasks, and the band rows'
 //       reached pixels and hole mask leave for global memory at once;
-//   P3  holes right of a row's last reached pixel take the fallback; the other holes
-//       are filled (Alg. 3, Eq. 6) by warps that take segments of the band's rows from
-//       a shared counter, one hole per lane, so a wide disocclusion is spread over many
-//       warps.  Hole edges and kernel candidates come from the bitmasks
-//       (leading/trailing-zero counts over 32-pixel words).
+//   P3a per band row: its last reached pixel, the border holes right of it (the
+//       fallback), and per word the counts of cracks and wider holes with prefix sums;
+//   P3b the other holes are filled (Alg. 3, Eq. 6) in chunks of 32 dealt to whichever
+//       warp is free, one hole per lane, so a wide disocclusion is spread over many
+//       warps; a chunk inside one hole is filled by the whole warp together.  Hole
+//       edges and kernel candidates come from the bitmasks (leading/trailing-zero
+//       counts over 32-pixel words).
 //
 // No thread ever waits on another CTA or on an asynchronous copy: the prefetches
 // only warm L2, and every read is an ordinary load.
