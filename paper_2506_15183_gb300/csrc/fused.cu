@@ -352,34 +352,42 @@ __device__ __forceinline__ void scatter_window(const FrameArgs& f, const float* 
 // here; their holes are written in P3.  The loads of a batch are unconditional (a hole
 // or a lane past the row end reads column 0, a batch row past the window reads the
 // last window row), so the batch has no branches around its loads.
-template <int RB, bool FULL>
+template <int RB, bool FULL, int NWI, int DX>
 __device__ __forceinline__ void resolve_batch(const FrameArgs& f, const float* depth, const uint32_t* color,
                                               const Window& s, int g, int j0, int nb, int jb0, int jb1,
                                               uint32_t near_m1, uint32_t far_m1)
 {
+    // NWI words of the row batch at once: word g and, if NWI == 2, word g + DX / 32
+    // (the next word the same warp owns), DX columns to the right.
     const int lane = threadIdx.x & 31;
     const int w = f.w, wpad = s.wpad;
     const int x = (g << 5) + lane;
-    const bool xin = x < w;
-    int sc[RB];
-    float zs[RB];
-    uint32_t cs[RB];
+    bool xin[NWI];
+#pragma unroll
+    for (int q = 0; q < NWI; ++q) xin[q] = x + q * DX < w;
+    int sc[NWI][RB];
+    float zs[NWI][RB];
+    uint32_t cs[NWI][RB];
     // offsets advance by one row stride per row: no multiplies in the batch
     int so = j0 * wpad + x;  // shared-memory word of (row, x)
     int go = j0 * w;         // global pixel offset of the row in the window
 #pragma unroll
     for (int u = 0; u < RB; ++u) {
-        sc[u] = ((FULL || u < nb) && xin) ? (int)s.zt[so] : -1;
+#pragma unroll
+        for (int q = 0; q < NWI; ++q) sc[q][u] = ((FULL || u < nb) && xin[q]) ? (int)s.zt[so + q * DX] : -1;
         so += wpad;
     }
 #pragma unroll
     for (int u = 0; u < RB; ++u) {
-        const int o = go + max(sc[u], 0);
-        zs[u] = 0.0f;
-        cs[u] = 0u;
-        if (FULL || u < nb) {
-            zs[u] = __ldg(depth + o);
-            cs[u] = __ldg(color + o);
+#pragma unroll
+        for (int q = 0; q < NWI; ++q) {
+            const int o = go + max(sc[q][u], 0);
+            zs[q][u] = 0.0f;
+            cs[q][u] = 0u;
+            if (FULL || u < nb) {
+                zs[q][u] = __ldg(depth + o);
+                cs[q][u] = __ldg(color + o);
+            }
         }
         go += w;
     }
@@ -389,16 +397,20 @@ __device__ __forceinline__ void resolve_batch(const FrameArgs& f, const float* d
     for (int u = 0; u < RB; ++u) {
         if (FULL || u < nb) {
             const int j = j0 + u;
-            const bool reached = sc[u] >= 0;
-            const uint32_t m = __ballot_sync(0xffffffffu, reached);
-            if (reached) {
-                s.zt[so] = clamped_depth_bits(zs[u], near_m1, far_m1);
-                s.rgba[so] = cs[u];
-            }
-            if (lane == 0) s.bits[j * s.nwords + g] = m;
-            if (j >= jb0 && j < jb1 && xin) {  // a band row: the pixel and its mask byte leave
-                if (reached) f.out[vo] = cs[u];
-                f.mask[vo] = reached ? 0 : 1;
+            const bool band = j >= jb0 && j < jb1;
+#pragma unroll
+            for (int q = 0; q < NWI; ++q) {
+                const bool reached = sc[q][u] >= 0;
+                const uint32_t m = __ballot_sync(0xffffffffu, reached);
+                if (reached) {
+                    s.zt[so + q * DX] = clamped_depth_bits(zs[q][u], near_m1, far_m1);
+                    s.rgba[so + q * DX] = cs[q][u];
+                }
+                if (lane == 0) s.bits[j * s.nwords + g + q * (DX >> 5)] = m;
+                if (band && xin[q]) {  // a band row: the pixel and its mask byte leave
+                    if (reached) f.out[vo + q * DX] = cs[q][u];
+                    f.mask[vo + q * DX] = reached ? 0 : 1;
+                }
             }
         }
         so += wpad;
@@ -410,14 +422,22 @@ template <int NT>
 __device__ __forceinline__ void resolve_window(const FrameArgs& f, const float* depth, const uint32_t* color,
                                                int nr, int y0, int y1, const Window& s)
 {
-    constexpr int NW = NT / 32, RB = 5;  // 15-row windows: three full batches (3..8 measured)
+    constexpr int NW = NT / 32, RB = 3;  // 15-row windows: five full batches (2..8 measured)
+    constexpr int DX = 32 * NW;          // columns between the two words a warp takes at once
     const int warp = threadIdx.x >> 5;
     const uint32_t near_m1 = __float_as_uint(f.near_) - 1u, far_m1 = __float_as_uint(f.far_) - 1u;
     const int jb0 = y0 - s.ra, jb1 = y1 - s.ra;  // band rows of the window: [jb0, jb1)
-    for (int g = warp; g < s.nwords; g += NW) {
+    for (int g = warp; g < s.nwords; g += 2 * NW) {
+        const bool two = g + NW < s.nwords;  // warp-uniform
         int j0 = 0;
-        for (; j0 + RB <= nr; j0 += RB) resolve_batch<RB, true>(f, depth, color, s, g, j0, RB, jb0, jb1, near_m1, far_m1);
-        if (j0 < nr) resolve_batch<RB, false>(f, depth, color, s, g, j0, nr - j0, jb0, jb1, near_m1, far_m1);
+        for (; j0 + RB <= nr; j0 += RB) {
+            if (two) resolve_batch<RB, true, 2, DX>(f, depth, color, s, g, j0, RB, jb0, jb1, near_m1, far_m1);
+            else resolve_batch<RB, true, 1, DX>(f, depth, color, s, g, j0, RB, jb0, jb1, near_m1, far_m1);
+        }
+        if (j0 < nr) {
+            if (two) resolve_batch<RB, false, 2, DX>(f, depth, color, s, g, j0, nr - j0, jb0, jb1, near_m1, far_m1);
+            else resolve_batch<RB, false, 1, DX>(f, depth, color, s, g, j0, nr - j0, jb0, jb1, near_m1, far_m1);
+        }
     }
 }
 
