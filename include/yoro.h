@@ -144,6 +144,20 @@ yoro_status yoro_synthesize_host(yoro_handle h, const void* host_color_rgba8, co
                                  void* cuda_stream);
 
 /*
+ * yoro_synthesize() on HOST buffers without staging copies (zero copy): the kernels load
+ * the left eye from and store the right eye and mask to page-locked host memory that is
+ * mapped into the device address space (cudaHostAlloc / cudaHostRegister with mapping;
+ * on systems with unified addressing every page-locked allocation is), over the
+ * host-device link (NVLink-C2C on Grace systems).  Each pointer is checked with
+ * cudaPointerGetAttributes: anything else returns YORO_EINVAL before any launch.  Same
+ * layout, alignment and result as yoro_synthesize; the L2 bulk prefetch of the inputs is
+ * not used.  Returns before the kernel finishes; synchronise the stream before reading.
+ */
+yoro_status yoro_synthesize_mapped(yoro_handle h, const void* host_color_rgba8, const float* host_depth_f32,
+                                   void* host_out_color_rgba8, unsigned char* host_out_hole_mask,
+                                   void* cuda_stream);
+
+/*
  * Synthesize n independent frames of possibly different sizes and cameras in one
  * persistent kernel launch (the same five steps per frame; results equal n calls of
  * yoro_synthesize).  frames: host array of n descriptors with device pointers; up to

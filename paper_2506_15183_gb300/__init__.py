@@ -18,7 +18,7 @@ __all__ = [
     "yoro_synthesize_unfused", "yoro_synthesize_host", "yoro_synthesize_batch", "yoro_stream_status",
     "yoro_max_fused_width", "yoro_status_string", "yoro_last_create_error", "STATUS",
     "yoro_synthesize_noalloc", "yoro_noalloc_max_pixels", "yoro_tune_batch", "yoro_batch_band",
-    "yoro_reset_tuning", "yoro_create_ex",
+    "yoro_reset_tuning", "yoro_create_ex", "yoro_synthesize_mapped",
 ]
 
 _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "libyoro.so")
@@ -65,7 +65,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.yoro_last_create_error.restype = I
     lib.yoro_destroy.argtypes = [P]
     lib.yoro_destroy.restype = None
-    for name in ("yoro_synthesize", "yoro_synthesize_unfused", "yoro_synthesize_host"):
+    for name in ("yoro_synthesize", "yoro_synthesize_unfused", "yoro_synthesize_host", "yoro_synthesize_mapped"):
         fn = getattr(lib, name)
         fn.argtypes = [P, P, P, P, P, P]
         fn.restype = I
@@ -198,6 +198,13 @@ def _frame_array(frames):
                         _dev_ptr(fr["out_color"], torch.uint8, (hh, w, 4), "out_color"),
                         _dev_ptr(fr["out_mask"], torch.uint8, (hh, w), "out_hole_mask"))
     return arr
+
+
+def yoro_synthesize_mapped(h: _Handle, color, depth, out_color, out_mask, stream=None) -> None:
+    """Host tensors in page-locked memory (``pin_memory()``), read and written by the kernel
+    directly (zero copy); synchronise before reading."""
+    p = _frame_ptrs(h, color, depth, out_color, out_mask, _host_ptr)
+    _check(load_library().yoro_synthesize_mapped(h.ptr, *p, _stream(stream)), "yoro_synthesize_mapped")
 
 
 def yoro_synthesize_batch(frames, stream=None) -> None:

@@ -216,6 +216,36 @@ yoro_status yoro_synthesize_unfused(yoro_handle c, const void* color, const floa
     return run_unfused(c, f, (cudaStream_t)stream);
 }
 
+yoro_status yoro_synthesize_mapped(yoro_handle c, const void* hcolor, const float* hdepth, void* hout,
+                                   unsigned char* hmask, void* stream)
+{
+    if (!c) return YORO_EINVAL;
+    if ((size_t)c->w * c->h == 0) return YORO_OK;
+    if (!hcolor || !hdepth || !hout || !hmask) return YORO_EINVAL;
+    yoro_status st = on_device(c);
+    if (st != YORO_OK) return st;
+    // Every buffer must be page-locked host memory mapped into the device address space:
+    // the kernels then load and store it directly, and nothing else is accepted.
+    const void* hp[4] = {hcolor, hdepth, hout, hmask};
+    void* dp[4];
+    for (int i = 0; i < 4; ++i) {
+        cudaPointerAttributes a;
+        if (cudaPointerGetAttributes(&a, hp[i]) != cudaSuccess || a.type != cudaMemoryTypeHost ||
+            !a.devicePointer) {
+            cudaGetLastError();
+            return YORO_EINVAL;
+        }
+        dp[i] = a.devicePointer;
+    }
+    FrameArgs f;
+    st = make_frame(c->w, c->h, c->k, c->near_, c->far_, dp[0], (const float*)dp[1], dp[2], (unsigned char*)dp[3],
+                    &f);
+    if (st != YORO_OK) return st;
+    f.bulk = 0;  // no L2 bulk prefetch of host memory
+    apply_options(c, &f);
+    return run_frame(c, f, (cudaStream_t)stream);
+}
+
 yoro_status yoro_synthesize_host(yoro_handle c, const void* hcolor, const float* hdepth, void* hout,
                                  unsigned char* hmask, void* stream)
 {

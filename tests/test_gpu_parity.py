@@ -255,6 +255,30 @@ def test_host_api_matches(yoro):
     yoro.yoro_destroy(hdl)
 
 
+def test_mapped_host_buffers(yoro):
+    """Zero copy: the kernels read and write page-locked host memory directly; pageable
+    host memory and device memory are refused before any launch."""
+    cfg = scene.quest_config()
+    c, d, _ = scene.render(cfg, 5)
+    cam = cfg.camera()
+    hdl = yoro.yoro_create(**cam)
+    hc = torch.from_numpy(c).pin_memory()
+    hd = torch.from_numpy(d).pin_memory()
+    ho = torch.zeros((cfg.h, cfg.w, 4), dtype=torch.uint8).pin_memory()
+    hm = torch.zeros((cfg.h, cfg.w), dtype=torch.uint8).pin_memory()
+    yoro.yoro_synthesize_mapped(hdl, hc, hd, ho, hm)
+    torch.cuda.synchronize()
+    _assert_same((ho.numpy(), hm.numpy()), _ref(c, d, cam), "mapped")
+    lib = yoro.load_library()
+    pageable = torch.from_numpy(c.copy())
+    assert lib.yoro_synthesize_mapped(hdl.ptr, pageable.data_ptr(), hd.data_ptr(), ho.data_ptr(), hm.data_ptr(),
+                                      None) == 1
+    dev = torch.from_numpy(d).to(DEV)
+    assert lib.yoro_synthesize_mapped(hdl.ptr, hc.data_ptr(), dev.data_ptr(), ho.data_ptr(), hm.data_ptr(),
+                                      None) == 1
+    yoro.yoro_destroy(hdl)
+
+
 def test_side_stream_and_two_handles(yoro):
     cfg = scene.small_config()
     s = torch.cuda.Stream()
