@@ -53,7 +53,7 @@ typedef enum {
     YORO_EALIGN = 2,   /* a pointer is not 4-byte aligned                                 */
     YORO_ENOMEM = 3,   /* a device or pinned-host allocation failed                       */
     YORO_ECUDA = 4,    /* a CUDA runtime call or kernel launch failed                     */
-    YORO_EDEVICE = 5,  /* reserved: a kernel reported an error                            */
+    YORO_EDEVICE = 5,  /* a kernel of the debug-bounds build skipped an out-of-range access */
     YORO_ETOOBIG = 6   /* the frame exceeds a limit of the requested entry point          */
 } yoro_status;
 
@@ -192,10 +192,30 @@ void yoro_reset_tuning(void);
 
 /*
  * Synchronise cuda_stream and report whether work on it failed: YORO_ECUDA if the
- * stream or the runtime reports a CUDA error, else YORO_OK.  h may be NULL (batch
- * launches have no handle).
+ * stream or the runtime reports a CUDA error; in the debug-bounds build YORO_EDEVICE if
+ * a kernel of this library recorded a skipped access since the last call (the record
+ * is cleared by reading it; it is device-wide, not per stream); else YORO_OK.  h may be
+ * NULL (batch launches have no handle).
  */
 yoro_status yoro_stream_status(yoro_handle h, void* cuda_stream);
+
+/*
+ * 1 if this library is the debug-bounds build, else 0.  That build compiles the same
+ * kernels with a range check in front of every shared- and global-memory access whose
+ * index is computed (source and target columns, window rows, hole positions, z-buffer
+ * keys); an access that fails its check is skipped, never made, and a code is OR-ed into
+ * a device status word that yoro_stream_status() reports.  No kernel traps.  The release
+ * build compiles the checks away.
+ */
+int yoro_debug_bounds_enabled(void);
+
+/*
+ * Launch, on cuda_stream, a one-warp kernel that records a code in the debug-bounds
+ * status word and touches no memory, so that a caller can see the reporting path work:
+ * yoro_stream_status() then returns YORO_EDEVICE once.  In the release build the kernel
+ * records nothing.  YORO_ECUDA if the launch fails.
+ */
+yoro_status yoro_debug_selftest(void* cuda_stream);
 
 /*
  * yoro_synthesize_unfused() without a handle and without allocating device memory, for

@@ -4,7 +4,9 @@ The functions below carry the names of the C ABI in ``include/yoro.h`` and only
 marshal arguments (tensor checks, pointers, streams); every step of the path runs
 in the library's CUDA kernels.  PyTorch supplies device memory and streams.  The
 library is loaded from ``paper_2506_15183_gb300/_lib/libyoro.so``; if it has not
-been built, every call raises ``RuntimeError`` (there is no CPU fallback).
+been built, every call raises ``RuntimeError`` (there is no CPU fallback).  A process
+that calls ``load_library(debug=True)`` before any other call uses the debug-bounds
+build ``libyoro_debug.so`` instead (``_build.build_cuda(debug=True)`` makes it).
 """
 from __future__ import annotations
 
@@ -18,10 +20,12 @@ __all__ = [
     "yoro_synthesize_unfused", "yoro_synthesize_host", "yoro_synthesize_batch", "yoro_stream_status",
     "yoro_max_fused_width", "yoro_status_string", "yoro_last_create_error", "STATUS",
     "yoro_synthesize_noalloc", "yoro_noalloc_max_pixels", "yoro_tune_batch", "yoro_batch_band",
-    "yoro_reset_tuning", "yoro_create_ex", "yoro_synthesize_mapped",
+    "yoro_reset_tuning", "yoro_create_ex", "yoro_synthesize_mapped", "yoro_debug_bounds_enabled",
+    "yoro_debug_selftest",
 ]
 
 _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "libyoro.so")
+_DEBUG_LIB_PATH = os.path.join(os.path.dirname(_LIB_PATH), "libyoro_debug.so")
 _lib = None
 
 STATUS = {0: "YORO_OK", 1: "YORO_EINVAL", 2: "YORO_EALIGN", 3: "YORO_ENOMEM", 4: "YORO_ECUDA",
@@ -47,12 +51,15 @@ class _Frame(ctypes.Structure):
                 ("out_color", ctypes.c_void_p), ("out_hole_mask", ctypes.c_void_p)]
 
 
-def load_library(path: str | None = None) -> ctypes.CDLL:
-    """Load libyoro.so (built by ``__graft_entry__.build()``); raise if it is missing."""
+def load_library(path: str | None = None, debug: bool = False) -> ctypes.CDLL:
+    """Load libyoro.so (built by ``__graft_entry__.build()``), or with ``debug`` the
+    debug-bounds build; raise if it is missing.  The first call decides for the process."""
     global _lib
     if _lib is not None:
+        if debug and not _lib.yoro_debug_bounds_enabled():
+            raise RuntimeError("the release library is already loaded in this process")
         return _lib
-    path = path or _LIB_PATH
+    path = path or (_DEBUG_LIB_PATH if debug else _LIB_PATH)
     if not os.path.exists(path):
         raise RuntimeError(f"libyoro.so not built ({path}); run __graft_entry__.build() first")
     lib = ctypes.CDLL(path)
@@ -87,6 +94,10 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.yoro_batch_band.restype = I
     lib.yoro_reset_tuning.argtypes = []
     lib.yoro_reset_tuning.restype = None
+    lib.yoro_debug_bounds_enabled.argtypes = []
+    lib.yoro_debug_bounds_enabled.restype = I
+    lib.yoro_debug_selftest.argtypes = [P]
+    lib.yoro_debug_selftest.restype = I
     _lib = lib
     return lib
 
@@ -255,6 +266,14 @@ def yoro_stream_status(h: _Handle | None, stream=None) -> int:
 
 def yoro_max_fused_width() -> int:
     return load_library().yoro_max_fused_width()
+
+
+def yoro_debug_bounds_enabled() -> bool:
+    return bool(load_library().yoro_debug_bounds_enabled())
+
+
+def yoro_debug_selftest(stream=None) -> None:
+    _check(load_library().yoro_debug_selftest(_stream(stream)), "yoro_debug_selftest")
 
 
 def yoro_status_string(code: int) -> str:

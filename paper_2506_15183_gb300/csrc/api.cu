@@ -462,7 +462,17 @@ yoro_status yoro_stream_status(yoro_handle c, void* stream)
         cudaGetLastError();
         return YORO_ECUDA;
     }
-    return cudaPeekAtLastError() == cudaSuccess ? YORO_OK : YORO_ECUDA;
+    if (cudaPeekAtLastError() != cudaSuccess) return YORO_ECUDA;
+    // both words are read (and cleared) whichever is set
+    const unsigned bad = yoro::fused_status_take() | yoro::unfused_status_take();
+    return bad ? YORO_EDEVICE : YORO_OK;
+}
+
+int yoro_debug_bounds_enabled(void) { return yoro::debug_bounds_built() ? 1 : 0; }
+
+yoro_status yoro_debug_selftest(void* stream)
+{
+    return yoro::debug_selftest_launch((cudaStream_t)stream) == cudaSuccess ? YORO_OK : YORO_ECUDA;
 }
 
 int yoro_max_fused_width(void)

@@ -38,6 +38,17 @@ namespace yoro {
 
 namespace {
 
+#ifdef YORO_DEBUG_BOUNDS
+__device__ unsigned g_status;  // debug-bounds status word of this file's kernels
+__device__ __forceinline__ void yoro_status_record(unsigned code) { atomicOr(&g_status, code); }
+#endif
+
+// Records kSelfTest in the debug-bounds build (no memory is touched); nothing otherwise.
+__global__ void selftest_kernel()
+{
+    if (threadIdx.x == 0) (void)YORO_BOUND(false, kSelfTest);
+}
+
 // Remaining weight below which the exact early exit is tested after each contribution
 // (2^-9: measured fastest among 2^-8 .. 2^-15 on the 1832x1920 workload).
 constexpr float kSettleFrom = 0.001953125f;
@@ -125,7 +136,7 @@ __device__ __forceinline__ uint32_t fill_from_edges(int x, int v, int L, int R, 
     const uint32_t mlo = ~0u << (R & 31);
 #pragma unroll 1
     for (int vv = v - ks.halo; vv <= v + ks.halo; ++vv) {
-        if (vv < 0 || vv >= h) continue;
+        if (vv < 0 || vv >= h || !YORO_BOUND(vv - s.ra >= 0 && vv - s.ra < s.slots, kBadHoles)) continue;
         const uint32_t* b = s.brow(vv);
         const uint32_t* zr = s.zrow(vv);
         const uint32_t* cr = s.crow(vv);
@@ -175,7 +186,8 @@ __device__ __forceinline__ uint32_t fill_hole_warp(int x, bool act, int v, int L
             const int c = ks.nearest ? R + g0 + lane : jhi - g0 - lane;
             bool contrib = false;
             uint32_t col = 0u;
-            if (ks.nearest ? c <= jhi : c >= R) {
+            if ((ks.nearest ? c <= jhi : c >= R) &&
+                YORO_BOUND(j >= 0 && j < s.slots && c >= 0 && c < s.wpad, kBadHoles)) {
                 const int i = j * s.wpad + c;
                 const bool reached = (s.bits[j * s.nwords + (c >> 5)] >> (c & 31)) & 1u;
                 contrib = reached && !(__uint_as_float(s.zt[i]) < d_occ);  // not foreground (O2)
@@ -202,7 +214,7 @@ __device__ __forceinline__ uint32_t fill_hole_warp(int x, bool act, int v, int L
             }
         }
     }
-    if (!done) res = f.any() ? f.result() : s.crow(v)[R];
+    if (!done) res = f.any() ? f.result() : (YORO_BOUND(R < s.wpad, kBadHoles) ? s.crow(v)[R] : 0u);
     return res;
 }
 
@@ -224,7 +236,8 @@ __device__ __forceinline__ uint32_t fill_crack(int x, int v, int h, int w, const
     for (int k = 0; k <= 2 * ks.halo; ++k) {
         const int vv = v - ks.halo + k;
         const bool row_in = vv >= 0 && vv < h;
-        const int vr = row_in ? vv : v;  // a valid row to read when vv is outside
+        // a valid row to read when vv is outside
+        const int vr = (row_in && YORO_BOUND(vv - s.ra >= 0 && vv - s.ra < s.slots, kBadHoles)) ? vv : v;
         const uint32_t* b = s.brow(vr);
         const uint32_t* zr = s.zrow(vr);
         const uint32_t* cr = s.crow(vr);
@@ -317,7 +330,8 @@ __device__ __forceinline__ void scatter_iter(const FrameArgs& f, const float* de
     for (int u = 0; u < U; ++u) {
         ru[u] = r;
         xu[u] = q;
-        z[u] = (FULL || i + u * NT < n) ? __ldg(depth + i + u * NT) : 0.0f;
+        z[u] = ((FULL || i + u * NT < n) && YORO_BOUND(i + u * NT < n, kBadScatter)) ? __ldg(depth + i + u * NT)
+                                                                                        : 0.0f;
         advance(r, q, dr, dq, w);
     }
 #pragma unroll
@@ -325,7 +339,8 @@ __device__ __forceinline__ void scatter_iter(const FrameArgs& f, const float* de
         if (FULL || i + u * NT < n) {
             uint32_t zb;
             const int xt = disparity_target(z[u], __fadd_rn((float)xu[u], 0.5f), f.k, near_m1, far_m1, f.half_m, zb);
-            if ((unsigned)xt < (unsigned)w) atomicMax(src + ru[u] * wpad + xt, xu[u]);
+            if ((unsigned)xt < (unsigned)w && YORO_BOUND(ru[u] * w + xu[u] < n, kBadScatter))
+                atomicMax(src + ru[u] * wpad + xt, xu[u]);
         }
     }
 }
@@ -354,7 +369,7 @@ __device__ __forceinline__ void scatter_window(const FrameArgs& f, const float* 
 // last window row), so the batch has no branches around its loads.
 template <int RB, bool FULL, int NWI, int DX>
 __device__ __forceinline__ void resolve_batch(const FrameArgs& f, const float* depth, const uint32_t* color,
-                                              const Window& s, int g, int j0, int nb, int jb0, int jb1,
+                                              const Window& s, int g, int j0, int nb, int nr, int jb0, int jb1,
                                               uint32_t near_m1, uint32_t far_m1)
 {
     // NWI words of the row batch at once: word g and, if NWI == 2, word g + DX / 32
@@ -374,7 +389,10 @@ __device__ __forceinline__ void resolve_batch(const FrameArgs& f, const float* d
 #pragma unroll
     for (int u = 0; u < RB; ++u) {
 #pragma unroll
-        for (int q = 0; q < NWI; ++q) sc[q][u] = ((FULL || u < nb) && xin[q]) ? (int)s.zt[so + q * DX] : -1;
+        for (int q = 0; q < NWI; ++q)
+            sc[q][u] = ((FULL || u < nb) && xin[q] && YORO_BOUND(so + q * DX < nr * wpad, kBadResolve))
+                           ? (int)s.zt[so + q * DX]
+                           : -1;
         so += wpad;
     }
 #pragma unroll
@@ -384,7 +402,7 @@ __device__ __forceinline__ void resolve_batch(const FrameArgs& f, const float* d
             const int o = go + max(sc[q][u], 0);
             zs[q][u] = 0.0f;
             cs[q][u] = 0u;
-            if (FULL || u < nb) {
+            if ((FULL || u < nb) && YORO_BOUND(o < nr * w, kBadResolve)) {
                 zs[q][u] = __ldg(depth + o);
                 cs[q][u] = __ldg(color + o);
             }
@@ -402,12 +420,14 @@ __device__ __forceinline__ void resolve_batch(const FrameArgs& f, const float* d
             for (int q = 0; q < NWI; ++q) {
                 const bool reached = sc[q][u] >= 0;
                 const uint32_t m = __ballot_sync(0xffffffffu, reached);
-                if (reached) {
+                if (reached && YORO_BOUND(so + q * DX < nr * wpad, kBadResolve)) {
                     s.zt[so + q * DX] = clamped_depth_bits(zs[q][u], near_m1, far_m1);
                     s.rgba[so + q * DX] = cs[q][u];
                 }
-                if (lane == 0) s.bits[j * s.nwords + g + q * (DX >> 5)] = m;
-                if (band && xin[q]) {  // a band row: the pixel and its mask byte leave
+                if (lane == 0 && YORO_BOUND(g + q * (DX >> 5) < s.nwords && j < nr, kBadResolve))
+                    s.bits[j * s.nwords + g + q * (DX >> 5)] = m;
+                // a band row: the pixel and its mask byte leave
+                if (band && xin[q] && YORO_BOUND(vo + q * DX < f.h * w, kBadResolve)) {
                     if (reached) f.out[vo + q * DX] = cs[q][u];
                     f.mask[vo + q * DX] = reached ? 0 : 1;
                 }
@@ -431,12 +451,14 @@ __device__ __forceinline__ void resolve_window(const FrameArgs& f, const float* 
         const bool two = g + NW < s.nwords;  // warp-uniform
         int j0 = 0;
         for (; j0 + RB <= nr; j0 += RB) {
-            if (two) resolve_batch<RB, true, 2, DX>(f, depth, color, s, g, j0, RB, jb0, jb1, near_m1, far_m1);
-            else resolve_batch<RB, true, 1, DX>(f, depth, color, s, g, j0, RB, jb0, jb1, near_m1, far_m1);
+            if (two) resolve_batch<RB, true, 2, DX>(f, depth, color, s, g, j0, RB, nr, jb0, jb1, near_m1, far_m1);
+            else resolve_batch<RB, true, 1, DX>(f, depth, color, s, g, j0, RB, nr, jb0, jb1, near_m1, far_m1);
         }
         if (j0 < nr) {
-            if (two) resolve_batch<RB, false, 2, DX>(f, depth, color, s, g, j0, nr - j0, jb0, jb1, near_m1, far_m1);
-            else resolve_batch<RB, false, 1, DX>(f, depth, color, s, g, j0, nr - j0, jb0, jb1, near_m1, far_m1);
+            if (two) resolve_batch<RB, false, 2, DX>(f, depth, color, s, g, j0, nr - j0, nr, jb0, jb1, near_m1,
+                                                     far_m1);
+            else resolve_batch<RB, false, 1, DX>(f, depth, color, s, g, j0, nr - j0, nr, jb0, jb1, near_m1,
+                                                     far_m1);
         }
     }
 }
@@ -564,7 +586,7 @@ __device__ __forceinline__ void run_band(const FrameArgs& f, int y0, int y1, Win
             const bool wide = chunk < ng;  // warp-uniform
             const int sh = wide ? 16 : 0;
             const int idx = ((wide ? chunk : chunk - ng) << 5) + lane;
-            const bool act = idx < (wide ? tg : tc);  // lane 0 is always active
+            bool act = idx < (wide ? tg : tc);  // lane 0 is always active
             int v = 0, x = 0;
             if (act) {
                 // band row: the last row whose offset is <= idx
@@ -591,6 +613,8 @@ __device__ __forceinline__ void run_band(const FrameArgs& f, int y0, int y1, Win
                 uint32_t cm, gm;
                 hole_masks(s.brow(v), g, nwords, lastr[vj], cm, gm);
                 x = (g << 5) + nth_set_bit(wide ? gm : cm, k);
+                // the located pixel is a hole of the band row (checked in the debug-bounds build)
+                act = YORO_BOUND((unsigned)x < (unsigned)w && !((s.brow(v)[x >> 5] >> (x & 31)) & 1u), kBadHoles);
             }
             uint32_t o = 0u;
             if (wide) {
@@ -606,7 +630,7 @@ __device__ __forceinline__ void run_band(const FrameArgs& f, int y0, int y1, Win
             } else if (act) {
                 o = fill_crack<VAR>(x, v, h, w, s, ks);
             }
-            if (act) f.out[(size_t)v * w + x] = o;
+            if (act && YORO_BOUND(v >= y0 && v < y1, kBadHoles)) f.out[(size_t)v * w + x] = o;
         }
     }
     __syncthreads();
@@ -670,6 +694,36 @@ constexpr int kSmall = 512;
 }  // namespace
 
 int fused_wpad(int w) { return ((w + 7) / 8) * 8; }
+
+unsigned fused_status_take()
+{
+#ifdef YORO_DEBUG_BOUNDS
+    unsigned v = 0, z = 0;
+    if (cudaMemcpyFromSymbol(&v, g_status, sizeof v) != cudaSuccess ||
+        cudaMemcpyToSymbol(g_status, &z, sizeof z) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return v;
+#else
+    return 0;
+#endif
+}
+
+cudaError_t debug_selftest_launch(cudaStream_t stream)
+{
+    selftest_kernel<<<1, 32, 0, stream>>>();
+    return cudaGetLastError();
+}
+
+bool debug_bounds_built()
+{
+#ifdef YORO_DEBUG_BOUNDS
+    return true;
+#else
+    return false;
+#endif
+}
 
 size_t fused_smem_bytes(int wpad, int band, int halo)
 {

@@ -21,6 +21,11 @@ namespace yoro {
 
 namespace {
 
+#ifdef YORO_DEBUG_BOUNDS
+__device__ unsigned g_status;  // debug-bounds status word of this file's kernels
+__device__ __forceinline__ void yoro_status_record(unsigned code) { atomicOr(&g_status, code); }
+#endif
+
 __global__ void scatter_kernel(FrameArgs f, unsigned long long* __restrict__ zbuf)
 {
     const size_t n = (size_t)f.w * (size_t)f.h;
@@ -30,13 +35,16 @@ __global__ void scatter_kernel(FrameArgs f, unsigned long long* __restrict__ zbu
         uint32_t zb;
         const int xt = disparity_target(f.depth[i], __fadd_rn((float)x, 0.5f), f.k, __float_as_uint(f.near_) - 1u,
                                         __float_as_uint(f.far_) - 1u, f.half_m, zb);
-        if (xt >= 0 && xt < f.w) atomicMin(&zbuf[(size_t)y * f.w + xt], zkey(zb, x));
+        if (xt >= 0 && xt < f.w && YORO_BOUND(y < f.h, kBadUnfused))
+            atomicMin(&zbuf[(size_t)y * f.w + xt], zkey(zb, x));
     }
 }
 
 __device__ __forceinline__ uint32_t key_color(const FrameArgs& f, int row, unsigned long long key)
 {
-    return f.color[(size_t)row * f.w + (uint32_t)key];
+    // the key's low word is a source column of the row (checked in the debug-bounds build)
+    const uint32_t c = (uint32_t)key;
+    return YORO_BOUND(c < (uint32_t)f.w && row >= 0 && row < f.h, kBadUnfused) ? f.color[(size_t)row * f.w + c] : 0u;
 }
 
 __global__ void resolve_fill_kernel(FrameArgs f, const unsigned long long* __restrict__ zbuf)
@@ -108,6 +116,21 @@ cudaError_t unfused_launch(const FrameArgs& f, unsigned long long* zbuf, cudaStr
     if (e != cudaSuccess) return e;
     resolve_fill_kernel<<<(unsigned)blocks, threads, 0, stream>>>(f, zbuf);
     return cudaGetLastError();
+}
+
+unsigned unfused_status_take()
+{
+#ifdef YORO_DEBUG_BOUNDS
+    unsigned v = 0, z = 0;
+    if (cudaMemcpyFromSymbol(&v, g_status, sizeof v) != cudaSuccess ||
+        cudaMemcpyToSymbol(g_status, &z, sizeof z) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return v;
+#else
+    return 0;
+#endif
 }
 
 }  // namespace yoro

@@ -8,6 +8,23 @@
 
 namespace yoro {
 
+// Debug-bounds build (-DYORO_DEBUG_BOUNDS): YORO_BOUND(cond, code) is true when cond
+// holds; otherwise it ORs `code` into the translation unit's device status word and is
+// false, and the caller skips the access it guards.  Nothing traps.  In release builds
+// it is the constant true and costs nothing.
+#ifdef YORO_DEBUG_BOUNDS
+#define YORO_BOUND(cond, code) ((cond) ? true : (yoro_status_record(code), false))
+#else
+#define YORO_BOUND(cond, code) true
+#endif
+
+// Codes of the status word (bits).
+constexpr unsigned kBadScatter = 1u;   // P1: depth load or target word outside the window
+constexpr unsigned kBadResolve = 2u;   // P2: window word, gather or output pixel out of range
+constexpr unsigned kBadHoles = 4u;     // P3a/P3b: hole bookkeeping or fill index out of range
+constexpr unsigned kBadUnfused = 8u;   // the z-buffer kernels
+constexpr unsigned kSelfTest = 16u;    // yoro_debug_selftest
+
 // One frame as the kernels see it.  color/out are RGBA8 pixels read as uint32.
 struct FrameArgs {
     const uint32_t* color;
@@ -60,6 +77,13 @@ cudaError_t fused_launch_batch(const BatchArgs& a, int wmax, const FusedLimits& 
 // api.cu: the camera checks of yoro_create, and the status yoro_last_create_error reports.
 bool camera_valid(int w, int h, float fx, float fy, float cx, float cy, float ipd, float near_, float far_);
 void set_last_create_error(int status);
+
+// Status words of the debug-bounds build (0 in release builds): read and cleared,
+// after the caller synchronised.  fused.cu also launches the self-test kernel.
+unsigned fused_status_take();
+unsigned unfused_status_take();
+cudaError_t debug_selftest_launch(cudaStream_t stream);
+bool debug_bounds_built();
 
 // unfused.cu: separate kernels around a global z-buffer of h*w keys.
 cudaError_t unfused_launch(const FrameArgs& f, unsigned long long* zbuf, cudaStream_t stream);

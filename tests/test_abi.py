@@ -4,6 +4,7 @@ import ctypes
 import os
 import re
 import subprocess
+import sys
 
 import pytest
 
@@ -46,6 +47,22 @@ def test_library_exports_every_declared_symbol(lib):
     for name in _declared():
         assert name in exported, name
         assert getattr(lib, name) is not None
+
+
+def test_debug_bounds_build_exports_the_same_boundary(lib):
+    """The debug-bounds variant builds from the same sources, exports every declared
+    entry point and says which build it is; the release library says it is not."""
+    from paper_2506_15183_gb300 import _build
+
+    path = _build.build_cuda(debug=True)
+    assert path == _build.DEBUG_LIB and path != _build.LIB
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\b(yoro_\w+)\b", out))
+    assert set(_declared()) <= exported
+    assert lib.yoro_debug_bounds_enabled() == 0
+    probe = "import ctypes, sys; print(ctypes.CDLL(sys.argv[1]).yoro_debug_bounds_enabled())"
+    r = subprocess.run([sys.executable, "-c", probe, path], capture_output=True, text=True)
+    assert r.returncode == 0 and r.stdout.strip() == "1", r.stderr
 
 
 def test_library_is_built_for_sm_103a(lib):
