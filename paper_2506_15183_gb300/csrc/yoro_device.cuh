@@ -123,27 +123,31 @@ struct FillAcc {
 
     // Exact early exit.  Every later step only grows acc and shrinks wrem: the updates
     // wrem -= wgt are exact (wrem/2 <= wgt <= wrem, Sterbenz; exact anyway among
-    // denormals), so the remaining weights sum to at most the current wrem; each later
-    // acc step adds at most 255 * wgt, and at most ~152 steps carry a non-zero weight
-    // (wrem at least halves per step), so rounding inflates the sum by less than a
-    // factor (1 + 2^-14).  The final quotient q = acc_N / (1 - wrem_N) therefore lies in
-    //     [acc, (acc + 255 wrem)(1 + 2^-14) / RN(1 - wrem)]
-    // (the lower end when every later color is 0).  Both ends are evaluated with
-    // upward rounding; if for every channel the interval stays below rint(acc) + 0.5,
-    // the rounded result is rint(acc) whatever the remaining candidates hold.
+    // denormals), so the remaining weights sum to at most the current wrem, and since
+    // wrem at least halves per step at most 150 later steps carry a non-zero weight.
+    // A later step adds y = RN(c * wgt) <= 255 wgt (1 + 2^-24) + 2^-150, and RN(acc + y)
+    // lies in [acc, acc + y + min(y, ulp/2)] (acc itself is a float no farther from
+    // acc + y than y, and acc < 256 keeps ulp/2 <= 2^-17).  With E = 255 (1 + 2^-24) wrem
+    // the final acc is therefore at most acc + E + min(E, 150 * 2^-17) + 300 * 2^-150, and the
+    // final denominator RN(1 - wrem_N) is at least RN(1 - wrem).  So the final quotient
+    // lies in [acc, (acc + E + min(E, 0.00115) + 1e-42) / RN(1 - wrem)] (the lower end
+    // when every later color is 0).  The upper end is evaluated with upward rounding; if
+    // for every channel it stays below rint(acc) + 0.5, the rounded result is rint(acc)
+    // whatever the remaining candidates hold.  The slack vanishes with wrem, so every
+    // pixel settles a few contributions after its acc is within reach of its result.
     __device__ __forceinline__ bool settled(uint32_t& out) const
     {
         const float den = __fsub_rn(1.0f, wrem);
         // rcp.approx is within 1 ulp of 1/den, so rcp * (1 + 2^-22) rounded up bounds it
         const float inv = __fmul_ru(rcp_approx(den), 1.0000002384185791f);
-        const float e = __fmul_ru(255.0f, wrem);
+        const float e1 = __fmul_ru(255.0000152587890625f, wrem);  // 255 + 2^-16 >= 255 (1 + 2^-24)
+        const float e = __fadd_ru(__fadd_ru(e1, fminf(e1, 0.00115f)), 1.0e-42f);
         uint32_t o = 0;
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
             const float r = rintf(acc[c]);
             if (r < 255.0f) {  // r >= 255: the clamped result is 255 whatever follows
-                const float s = __fadd_ru(__fmul_ru(__fadd_ru(acc[c], e), 1.00006103515625f), 1.0e-18f);
-                const float hi = __fmul_ru(s, inv);
+                const float hi = __fmul_ru(__fadd_ru(acc[c], e), inv);
                 if (!(hi < __fadd_rn(r, 0.5f))) return false;
             }
             o |= (uint32_t)fminf(r, 255.0f) << (8 * c);
