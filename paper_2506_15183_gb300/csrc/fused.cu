@@ -480,9 +480,11 @@ __device__ __forceinline__ void run_band(const FrameArgs& f, int y0, int y1, Win
     const float* depth = f.depth + (size_t)ra * w;
     const uint32_t* color = f.color + (size_t)ra * w;
 
-    if (f.bulk && warp == 0) {  // depth first: P1 needs it before P2 needs color
-        for (int j = lane; j < nr; j += 32) prefetch_l2(depth + (size_t)j * w, (uint32_t)w * 4u);
-        for (int j = lane; j < nr; j += 32) prefetch_l2(color + (size_t)j * w, (uint32_t)w * 4u);
+    if (f.bulk && lane == 0) {  // one depth row, then its color row, per warp
+        for (int j = warp; j < nr; j += NW) {
+            prefetch_l2(depth + (size_t)j * w, (uint32_t)w * 4u);
+            prefetch_l2(color + (size_t)j * w, (uint32_t)w * 4u);
+        }
     }
     {
         uint4* z4 = reinterpret_cast<uint4*>(s.zt);  // four words per 16 bytes; wpad % 8 == 0

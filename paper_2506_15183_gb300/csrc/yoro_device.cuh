@@ -78,6 +78,14 @@ __device__ __forceinline__ unsigned long long zkey(uint32_t zbits, int x)
     return ((unsigned long long)zbits << 32) | (unsigned)x;
 }
 
+// A channel byte of an RGBA8 word as a float: the byte is put under the exponent of
+// 2^23 (the float 2^23 + byte, exactly) and 2^23 is subtracted, which is exact; equal
+// to __uint2float_rn of the byte, without the conversion unit.
+__device__ __forceinline__ float channel(uint32_t rgba, uint32_t sel)
+{
+    return __fsub_rn(__uint_as_float(__byte_perm(rgba, 0x4B00u, sel)), 8388608.0f);
+}
+
 // Accumulator of the Patcher (Alg. 3) for one hole pixel.
 struct FillAcc {
     float acc[4];
@@ -89,6 +97,15 @@ struct FillAcc {
         wrem = 1.0f;
         t = t_;
     }
+    // Each channel sum += channel * wgt (multiply, then add: never fused), wrem -= wgt.
+    __device__ __forceinline__ void step(uint32_t rgba, float wgt)
+    {
+        acc[0] = __fadd_rn(acc[0], __fmul_rn(channel(rgba, 0x5440u), wgt));
+        acc[1] = __fadd_rn(acc[1], __fmul_rn(channel(rgba, 0x5441u), wgt));
+        acc[2] = __fadd_rn(acc[2], __fmul_rn(channel(rgba, 0x5442u), wgt));
+        acc[3] = __fadd_rn(acc[3], __fmul_rn(channel(rgba, 0x5443u), wgt));
+        wrem = __fsub_rn(wrem, wgt);
+    }
     // One contributing candidate of color `rgba`.  Eq. 6: wgt = wrem/2 + 0.3 wrem t,
     // evaluated (wrem * 0.5) + ((0.3 * wrem) * t).  Returns false once wgt == 0: from
     // then on wgt stays 0 and acc/wrem are unchanged (acc + c*0 == acc, wrem - 0 ==
@@ -99,11 +116,7 @@ struct FillAcc {
         const float b = __fmul_rn(__fmul_rn(0.3f, wrem), t);
         const float wgt = __fadd_rn(a, b);
         if (wgt == 0.0f) return false;
-        acc[0] = __fadd_rn(acc[0], __fmul_rn(__uint2float_rn(rgba & 255u), wgt));
-        acc[1] = __fadd_rn(acc[1], __fmul_rn(__uint2float_rn((rgba >> 8) & 255u), wgt));
-        acc[2] = __fadd_rn(acc[2], __fmul_rn(__uint2float_rn((rgba >> 16) & 255u), wgt));
-        acc[3] = __fadd_rn(acc[3], __fmul_rn(__uint2float_rn(rgba >> 24), wgt));
-        wrem = __fsub_rn(wrem, wgt);
+        step(rgba, wgt);
         return true;
     }
     // add(rgba) when `take`, else nothing: a weight of exactly 0 leaves acc (acc + c*0)
@@ -112,12 +125,7 @@ struct FillAcc {
     {
         const float a = __fmul_rn(wrem, 0.5f);
         const float b = __fmul_rn(__fmul_rn(0.3f, wrem), t);
-        const float wgt = take ? __fadd_rn(a, b) : 0.0f;
-        acc[0] = __fadd_rn(acc[0], __fmul_rn(__uint2float_rn(rgba & 255u), wgt));
-        acc[1] = __fadd_rn(acc[1], __fmul_rn(__uint2float_rn((rgba >> 8) & 255u), wgt));
-        acc[2] = __fadd_rn(acc[2], __fmul_rn(__uint2float_rn((rgba >> 16) & 255u), wgt));
-        acc[3] = __fadd_rn(acc[3], __fmul_rn(__uint2float_rn(rgba >> 24), wgt));
-        wrem = __fsub_rn(wrem, wgt);
+        step(rgba, take ? __fadd_rn(a, b) : 0.0f);
     }
     __device__ __forceinline__ bool any() const { return wrem != 1.0f; }
 
