@@ -56,6 +56,8 @@ def _load():
         lib.oracle_fill_ex.restype = None
         lib.oracle_synthesize_ex.argtypes = [I, I, F, F, F, F, F, F, F, P, P, I, I, P, P]
         lib.oracle_synthesize_ex.restype = I
+        lib.oracle_synthesize_imb.argtypes = [I, I, F, F, F, F, P, P, I, I, I, I, P, P]
+        lib.oracle_synthesize_imb.restype = I
         _lib = lib
     return _lib
 
@@ -136,6 +138,25 @@ def synthesize(color, depth, fx, fy, cx, cy, ipd, near, far, kernel_rows=3, near
                                       out.ctypes.data, mask.ctypes.data)
     if rc != 0:
         raise RuntimeError(f"oracle_synthesize failed ({rc})")
+    return out, mask
+
+
+def synthesize_imb(color, depth, fx, ipd, near, far, div, interp, kernel_rows=3, nearest_first=False):
+    """The path with the row-downsampled intermediate buffer of strategies (c) and (d):
+    a reprojection at 1/div of the row resolution (div in 1, 2, 4, 8, 16) and, with
+    interp, the shift interpolated between cells and the color sampled linearly."""
+    color = _c(color, np.uint8)
+    depth = _c(depth, np.float32)
+    h, w = depth.shape
+    if color.shape != (h, w, 4):
+        raise ValueError("color must be uint8[H,W,4] matching depth")
+    out = np.empty((h, w, 4), np.uint8)
+    mask = np.empty((h, w), np.uint8)
+    rc = _load().oracle_synthesize_imb(w, h, fx, ipd, near, far, color.ctypes.data, depth.ctypes.data, int(div),
+                                       int(bool(interp)), int(kernel_rows), int(bool(nearest_first)),
+                                       out.ctypes.data, mask.ctypes.data)
+    if rc != 0:
+        raise RuntimeError(f"oracle_synthesize_imb failed ({rc})")
     return out, mask
 
 

@@ -320,3 +320,150 @@ int oracle_synthesize(int w, int h, float fx, float fy, float cx, float cy, floa
 {
     return oracle_synthesize_ex(w, h, fx, fy, cx, cy, ipd, near_, far_, color, depth, 3, 0, out_color, mask);
 }
+
+/*
+ * Strategies (c) and (d) of the Reprojector: the resolution-independent intermediate
+ * buffer (ImBuffer) downsampled along the row, and the optional linear interpolation.
+ * The paper gives only their intent (the ImBuffer "records the distance the pixel
+ * shifts", the full-resolution image "is sampled based on linear interpolation of the
+ * distance shifted", and a non-hole pixel takes "the color sampled from the
+ * full-resolution rendered image, using the location provided by the ImBuffer"); the
+ * reading written out here:
+ *
+ *   s = div in {1, 2, 4, 8, 16} (1/2 .. 1/16 of the per-eye resolution, along the row:
+ *   the warp moves pixels along rows only, O1, so rows stay at full resolution).
+ *   Row y has ws = ceil(w / s) cells; cell i stands for source pixels s i .. s i + s - 1.
+ *
+ *   1. Algorithm 1 per cell, on its representative pixel p = min(s i + s/2, w - 1):
+ *      zc = clamp(depth(y, p)) as in oracle_disparity, disp = k / zc,
+ *      t = (p + 0.5) - disp, target cell floor(t / s) (dropped outside [0, ws)).
+ *   2. Algorithm 2 per row over the cells: nearest kept, the first on equal depth.
+ *      A target cell records its winner's cell i, zc and disp (the shift).
+ *   3. Full resolution: pixel x lies in cell j = floor(x / s); it is a hole if that
+ *      cell is, otherwise its depth is the winner's zc and its color
+ *        interp = 0: the source pixel at the same place in the winning cell,
+ *                    min(s i + (x - s j), w - 1);
+ *        interp = 1: the shift D linearly between cell j's and the neighbouring cell's
+ *                    on the side of the pixel centre x + 0.5 (weight |x + 0.5 - c_j| / s
+ *                    with c_j = s j + s/2 the cell centre; D = disp_j if that neighbour is
+ *                    a hole or outside the row); the color sampled at texel coordinate
+ *                    u = x + D (texel centres at integers): clamped to the row's first or
+ *                    last texel outside [0, w - 1], otherwise c0 + (c1 - c0) f between the
+ *                    texels floor(u) and floor(u) + 1 with f = u - floor(u), per channel,
+ *                    rounded half to even.
+ *   4. Algorithm 3 with Eq. 6 at full resolution over that image (oracle_hole_edges,
+ *      oracle_fill_ex), its reached pixels the candidates.
+ *
+ * With s = 1 and interp = 0 every step is the base path's, so the result equals
+ * oracle_synthesize_ex's.  Returns 0, -1 on bad arguments, -2 if a temporary could
+ * not be allocated.
+ */
+int oracle_synthesize_imb(int w, int h, float fx, float ipd, float near_, float far_, const uint8_t* color,
+                          const float* depth, int div, int interp, int kernel_rows, int nearest_first,
+                          uint8_t* out_color, uint8_t* mask)
+{
+    if (w < 0 || h < 0 || kernel_rows < 1 || (kernel_rows & 1) == 0) return -1;
+    if (div != 1 && div != 2 && div != 4 && div != 8 && div != 16) return -1;
+    if (interp != 0 && interp != 1) return -1;
+    size_t n = (size_t)w * (size_t)h;
+    if (n == 0) return 0;
+    const int ws = (w + div - 1) / div;
+    const float k = fx * ipd;
+    const size_t nc = (size_t)ws * (size_t)h;
+    int32_t* win = (int32_t*)malloc(nc * sizeof(int32_t));  /* winner cell, or -1 */
+    float* wz = (float*)malloc(nc * sizeof(float));        /* winner's zc */
+    float* wd = (float*)malloc(nc * sizeof(float));        /* winner's disp */
+    int32_t* src = (int32_t*)malloc(n * sizeof(int32_t));  /* full resolution: >= 0 reached */
+    float* zt = (float*)malloc(n * sizeof(float));
+    int32_t* L = (int32_t*)malloc(n * sizeof(int32_t));
+    int32_t* R = (int32_t*)malloc(n * sizeof(int32_t));
+    uint8_t* warped = (uint8_t*)malloc(n * 4);
+    int rc = 0;
+    if (!win || !wz || !wd || !src || !zt || !L || !R || !warped) {
+        rc = -2;
+        goto done;
+    }
+    for (int y = 0; y < h; ++y) {
+        int32_t* wrow = win + (size_t)y * (size_t)ws;
+        float* zrow = wz + (size_t)y * (size_t)ws;
+        float* drow = wd + (size_t)y * (size_t)ws;
+        for (int j = 0; j < ws; ++j) wrow[j] = -1;
+        /* steps 1 and 2: the cells of the row, scanned left to right */
+        for (int i = 0; i < ws; ++i) {
+            int p = div * i + div / 2;
+            if (p > w - 1) p = w - 1;
+            float z = depth[(size_t)y * (size_t)w + (size_t)p];
+            if (!(z > 0.0f) || isinf(z)) z = far_;
+            float c = fminf(fmaxf(z, near_), far_);
+            float disp = k / c;
+            float t = ((float)p + 0.5f) - disp;
+            float tc = floorf(t / (float)div);
+            if (!(tc >= 0.0f && tc < (float)ws)) continue;
+            int j = (int)tc;
+            if (wrow[j] < 0 || c < zrow[j]) {
+                wrow[j] = i;
+                zrow[j] = c;
+                drow[j] = disp;
+            }
+        }
+        /* step 3: full resolution */
+        for (int x = 0; x < w; ++x) {
+            size_t q = (size_t)y * (size_t)w + (size_t)x;
+            int j = x / div;
+            if (wrow[j] < 0) {
+                src[q] = -1;
+                zt[q] = INFINITY;
+                memset(warped + 4 * q, 0, 4);
+                mask[q] = 1;
+                continue;
+            }
+            src[q] = 0;
+            zt[q] = zrow[j];
+            mask[q] = 0;
+            const uint8_t* crow = color + 4 * (size_t)y * (size_t)w;
+            if (!interp) {
+                int sx = div * wrow[j] + (x - div * j);
+                if (sx > w - 1) sx = w - 1;
+                memcpy(warped + 4 * q, crow + 4 * (size_t)sx, 4);
+                continue;
+            }
+            float centre = (float)(div * j) + 0.5f * (float)div;
+            float off = ((float)x + 0.5f) - centre;
+            int nb = off < 0.0f ? j - 1 : j + 1;
+            float D = drow[j];
+            if (off != 0.0f && nb >= 0 && nb < ws && wrow[nb] >= 0) {
+                float a = fabsf(off) / (float)div;
+                D = drow[j] + (drow[nb] - drow[j]) * a;
+            }
+            float u = (float)x + D;
+            if (u <= 0.0f) {
+                memcpy(warped + 4 * q, crow, 4);
+            } else if (u >= (float)(w - 1)) {
+                memcpy(warped + 4 * q, crow + 4 * (size_t)(w - 1), 4);
+            } else {
+                float fl = floorf(u);
+                int i0 = (int)fl;
+                float f = u - fl;
+                for (int ch = 0; ch < 4; ++ch) {
+                    float c0 = (float)crow[4 * (size_t)i0 + ch];
+                    float c1 = (float)crow[4 * (size_t)(i0 + 1) + ch];
+                    float v = c0 + (c1 - c0) * f;
+                    warped[4 * q + ch] = (uint8_t)rintf(v);
+                }
+            }
+        }
+    }
+    /* step 4 */
+    oracle_hole_edges(w, h, src, L, R);
+    oracle_fill_ex(w, h, src, zt, L, R, warped, kernel_rows, nearest_first, out_color);
+done:
+    free(win);
+    free(wz);
+    free(wd);
+    free(src);
+    free(zt);
+    free(L);
+    free(R);
+    free(warped);
+    return rc;
+}
