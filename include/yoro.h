@@ -100,8 +100,33 @@ yoro_handle yoro_create(int w, int h, float fx, float fy, float cx, float cy, fl
 yoro_handle yoro_create_ex(int w, int h, float fx, float fy, float cx, float cy, float ipd, float near_,
                            float far_, const yoro_options* opt);
 
-/* Status of the last yoro_create() / yoro_create_ex() on the calling thread (YORO_OK
- * after a success). */
+/*
+ * yoro_create_ex() with the Reprojector's row-downsampled intermediate buffer
+ * (strategies (c) and (d) of the paper: an ImBuffer at 1/2 .. 1/16 of the per-eye
+ * resolution, "sampled based on linear interpolation of the distance shifted").  The
+ * paper gives their intent only; the reading implemented:
+ *   imbuffer_div s in {1, 2, 4, 8, 16}: each row is reprojected in cells of s source
+ *     pixels (ceil(w / s) per row): a cell's depth is that of its pixel
+ *     min(s i + s/2, w - 1), its target cell floor(((p + 0.5) - k / zc) / s), the
+ *     nearest source cell kept per target cell, which records its shift k / zc;
+ *   interpolate 0: a right-eye pixel copies the pixel at the same place in its cell's
+ *     winning cell; 1: the source is sampled linearly (per channel, rounded half to
+ *     even) at x + D, D the shift interpolated between the pixel's cell and the
+ *     neighbouring cell on the side of the pixel centre, clamped to the row's ends;
+ *   a pixel whose cell no source cell reaches is a hole, filled by the Patcher at full
+ *   resolution (the handle's kernel variant) from the reached pixels, whose depth is
+ *   their winning cell's.
+ * s = 1 without interpolation is the base path.  Every synthesize call of the handle
+ * (fused, unfused, host, mapped) takes this path when s > 1 or interpolate = 1: three
+ * launches around handle-owned scratch memory (8 ceil(w/s) h + 4 w h bytes, allocated
+ * on the first call).  Returns NULL with YORO_EINVAL for another s or interpolate, and
+ * as yoro_create_ex() otherwise.
+ */
+yoro_handle yoro_create_imb(int w, int h, float fx, float fy, float cx, float cy, float ipd, float near_,
+                            float far_, const yoro_options* opt, int imbuffer_div, int interpolate);
+
+/* Status of the last yoro_create() / yoro_create_ex() / yoro_create_imb() on the
+ * calling thread (YORO_OK after a success). */
 yoro_status yoro_last_create_error(void);
 
 /* Release the handle and the device memory it owns.  NULL is accepted.  Pending work

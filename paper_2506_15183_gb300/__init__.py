@@ -21,7 +21,7 @@ __all__ = [
     "yoro_max_fused_width", "yoro_status_string", "yoro_last_create_error", "STATUS",
     "yoro_synthesize_noalloc", "yoro_noalloc_max_pixels", "yoro_tune_batch", "yoro_batch_band",
     "yoro_reset_tuning", "yoro_create_ex", "yoro_synthesize_mapped", "yoro_debug_bounds_enabled",
-    "yoro_debug_selftest",
+    "yoro_debug_selftest", "yoro_create_imb",
 ]
 
 _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "libyoro.so")
@@ -68,6 +68,8 @@ def load_library(path: str | None = None, debug: bool = False) -> ctypes.CDLL:
     lib.yoro_create.restype = P
     lib.yoro_create_ex.argtypes = [I, I, F, F, F, F, F, F, F, ctypes.POINTER(_Options)]
     lib.yoro_create_ex.restype = P
+    lib.yoro_create_imb.argtypes = [I, I, F, F, F, F, F, F, F, ctypes.POINTER(_Options), I, I]
+    lib.yoro_create_imb.restype = P
     lib.yoro_last_create_error.argtypes = []
     lib.yoro_last_create_error.restype = I
     lib.yoro_destroy.argtypes = [P]
@@ -167,6 +169,20 @@ def yoro_create_ex(w, h, fx, fy, cx, cy, ipd, near, far, kernel_rows=3, nearest_
     p = lib.yoro_create_ex(int(w), int(h), fx, fy, cx, cy, ipd, near, far, ctypes.byref(opt))
     if not p:
         raise YoroError(lib.yoro_last_create_error(), "yoro_create_ex")
+    return _Handle(p, int(w), int(h))
+
+
+def yoro_create_imb(w, h, fx, fy, cx, cy, ipd, near, far, kernel_rows=3, nearest_first=False, imbuffer_div=1,
+                    interpolate=False) -> _Handle:
+    """yoro_create_ex through the row-downsampled intermediate buffer: cells of
+    imbuffer_div pixels (1, 2, 4, 8, 16) and, with interpolate, the shift interpolated
+    between cells and the source sampled linearly."""
+    lib = load_library()
+    opt = _Options(int(kernel_rows), int(bool(nearest_first)))
+    p = lib.yoro_create_imb(int(w), int(h), fx, fy, cx, cy, ipd, near, far, ctypes.byref(opt), int(imbuffer_div),
+                            int(bool(interpolate)))
+    if not p:
+        raise YoroError(lib.yoro_last_create_error(), "yoro_create_imb")
     return _Handle(p, int(w), int(h))
 
 
@@ -283,9 +299,13 @@ def yoro_status_string(code: int) -> str:
 class Synthesizer:
     """Owns a handle for one camera; ``__call__`` allocates the outputs with torch."""
 
-    def __init__(self, w, h, fx, fy, cx, cy, ipd, near=0.05, far=1000.0, kernel_rows=3, nearest_first=False):
+    def __init__(self, w, h, fx, fy, cx, cy, ipd, near=0.05, far=1000.0, kernel_rows=3, nearest_first=False,
+                 imbuffer_div=1, interpolate=False):
         self.w, self.h = int(w), int(h)
-        if kernel_rows == 3 and not nearest_first:
+        if imbuffer_div != 1 or interpolate:
+            self.handle = yoro_create_imb(w, h, fx, fy, cx, cy, ipd, near, far, kernel_rows, nearest_first,
+                                          imbuffer_div, interpolate)
+        elif kernel_rows == 3 and not nearest_first:
             self.handle = yoro_create(w, h, fx, fy, cx, cy, ipd, near, far)
         else:
             self.handle = yoro_create_ex(w, h, fx, fy, cx, cy, ipd, near, far, kernel_rows, nearest_first)

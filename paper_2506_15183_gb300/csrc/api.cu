@@ -24,11 +24,13 @@ struct yoro_ctx {
     float k;
     int device;
     int halo, nearest;  // Patcher kernel shape (yoro_options)
+    int imb_div, imb_interp;  // row-downsampled intermediate buffer (yoro_create_imb)
     bool fused_ok;      // the window of one band row fits shared memory
     FusedLimits lim;
     yoro::FusedShape shape;
     unsigned long long* d_zbuf;    // unfused path, h*w keys, allocated on first use
     unsigned char* d_stage;        // host-buffer path, 13*h*w bytes (+ padding), on first use
+    void* d_imb;                   // intermediate-buffer path: cell keys and depths, on first use
 };
 
 namespace {
@@ -114,8 +116,25 @@ yoro_status run_unfused(yoro_ctx* c, const FrameArgs& f, cudaStream_t s)
     return yoro::unfused_launch(f, c->d_zbuf, s) == cudaSuccess ? YORO_OK : YORO_ECUDA;
 }
 
+// The handle's frames through the row-downsampled intermediate buffer.
+yoro_status run_imb(yoro_ctx* c, const FrameArgs& f, cudaStream_t s)
+{
+    if (!c->d_imb) {
+        if (cudaMalloc(&c->d_imb, yoro::imb_scratch_bytes(c->w, c->h, c->imb_div)) != cudaSuccess) {
+            c->d_imb = nullptr;
+            cudaGetLastError();
+            return YORO_ENOMEM;
+        }
+    }
+    const yoro::ImbArgs a = yoro::imb_args(c->d_imb, c->w, c->h, c->imb_div, c->imb_interp);
+    return yoro::imb_launch(f, a, s) == cudaSuccess ? YORO_OK : YORO_ECUDA;
+}
+
+bool uses_imb(const yoro_ctx* c) { return c->imb_div > 1 || c->imb_interp; }
+
 yoro_status run_frame(yoro_ctx* c, FrameArgs f, cudaStream_t s)
 {
+    if (uses_imb(c)) return run_imb(c, f, s);
     if (!c->fused_ok) return run_unfused(c, f, s);
     f.band = c->shape.band;
     return yoro::fused_launch(f, c->lim, c->shape.two_per_sm, s) == cudaSuccess ? YORO_OK : YORO_ECUDA;
@@ -171,10 +190,27 @@ yoro_handle yoro_create_ex(int w, int h, float fx, float fy, float cx, float cy,
     }
     c->halo = (kernel_rows - 1) / 2;
     c->nearest = nearest;
+    c->imb_div = 1;
+    c->imb_interp = 0;
     c->fused_ok = w <= c->lim.max_width &&
                   yoro::fused_smem_bytes(yoro::fused_wpad(w), 1, c->halo) <= (size_t)c->lim.smem_per_block;
     c->shape = yoro::fused_shape(c->lim, w, h, c->halo);
     g_last_create = YORO_OK;
+    return c;
+}
+
+yoro_handle yoro_create_imb(int w, int h, float fx, float fy, float cx, float cy, float ipd, float near_, float far_,
+                            const yoro_options* opt, int imbuffer_div, int interpolate)
+{
+    if ((imbuffer_div != 1 && imbuffer_div != 2 && imbuffer_div != 4 && imbuffer_div != 8 && imbuffer_div != 16) ||
+        (interpolate != 0 && interpolate != 1)) {
+        g_last_create = YORO_EINVAL;
+        return nullptr;
+    }
+    yoro_ctx* c = yoro_create_ex(w, h, fx, fy, cx, cy, ipd, near_, far_, opt);
+    if (!c) return nullptr;
+    c->imb_div = imbuffer_div;
+    c->imb_interp = interpolate;
     return c;
 }
 
@@ -185,6 +221,7 @@ void yoro_destroy(yoro_handle c)
     if (!c) return;
     if (c->d_zbuf) cudaFree(c->d_zbuf);
     if (c->d_stage) cudaFree(c->d_stage);
+    if (c->d_imb) cudaFree(c->d_imb);
     delete c;
 }
 
@@ -213,6 +250,7 @@ yoro_status yoro_synthesize_unfused(yoro_handle c, const void* color, const floa
     st = make_frame(c->w, c->h, c->k, c->near_, c->far_, color, depth, out_color, out_mask, &f);
     if (st != YORO_OK) return st;
     apply_options(c, &f);
+    if (uses_imb(c)) return run_imb(c, f, (cudaStream_t)stream);
     return run_unfused(c, f, (cudaStream_t)stream);
 }
 
@@ -464,7 +502,7 @@ yoro_status yoro_stream_status(yoro_handle c, void* stream)
     }
     if (cudaPeekAtLastError() != cudaSuccess) return YORO_ECUDA;
     // both words are read (and cleared) whichever is set
-    const unsigned bad = yoro::fused_status_take() | yoro::unfused_status_take();
+    const unsigned bad = yoro::fused_status_take() | yoro::unfused_status_take() | yoro::imb_status_take();
     return bad ? YORO_EDEVICE : YORO_OK;
 }
 

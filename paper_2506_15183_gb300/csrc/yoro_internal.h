@@ -24,6 +24,7 @@ constexpr unsigned kBadResolve = 2u;   // P2: window word, gather or output pixe
 constexpr unsigned kBadHoles = 4u;     // P3a/P3b: hole bookkeeping or fill index out of range
 constexpr unsigned kBadUnfused = 8u;   // the z-buffer kernels
 constexpr unsigned kSelfTest = 16u;    // yoro_debug_selftest
+constexpr unsigned kBadImb = 32u;      // row-downsampled intermediate buffer kernels
 
 // One frame as the kernels see it.  color/out are RGBA8 pixels read as uint32.
 struct FrameArgs {
@@ -87,5 +88,17 @@ bool debug_bounds_built();
 
 // unfused.cu: separate kernels around a global z-buffer of h*w keys.
 cudaError_t unfused_launch(const FrameArgs& f, unsigned long long* zbuf, cudaStream_t stream);
+
+// The row-downsampled intermediate buffer (imbuffer.cu): div source pixels per cell
+// (1, 2, 4, 8 or 16), linear interpolation of the shift and the color when interp.
+struct ImbArgs {
+    unsigned long long* cells;  // h * ws keys (clamped depth bits << 32 | source cell)
+    float* zt;                  // h * w depths of the reached pixels
+    int div, interp, ws;
+};
+size_t imb_scratch_bytes(int w, int h, int div);
+ImbArgs imb_args(void* scratch, int w, int h, int div, int interp);
+cudaError_t imb_launch(const FrameArgs& f, const ImbArgs& a, cudaStream_t stream);
+unsigned imb_status_take();
 
 }  // namespace yoro

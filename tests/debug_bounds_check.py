@@ -3,8 +3,8 @@
 Run by ``test_gpu_debug_bounds.py`` as ``python tests/debug_bounds_check.py``: the
 process loads the debug-bounds library before any other call, synthesizes frames that
 exercise every kernel (fused single-frame launch with the default and variant kernels,
-the batch launch, the unfused launch; tall bands, ragged widths, a wide-disparity
-camera), and checks for each that the status word stayed clear (no range check failed)
+the batch launch, the unfused launch, the intermediate-buffer launches; tall bands,
+ragged widths, a wide-disparity camera), and checks for each that the status word stayed clear (no range check failed)
 and that the result still equals the CPU oracle byte for byte.  Then the self-test
 kernel must raise ``YORO_EDEVICE`` exactly once.  Prints ``debug-bounds OK`` at the end.
 """
@@ -83,6 +83,18 @@ def main() -> None:
         _single(c, d, cam, what=f"{w}x{h}")
     c, d, cam = _ragged(64, 777, 9, ipd=2.0, fx=5000.0)  # targets far outside the frame
     _single(c, d, cam, what="wide disparity")
+
+    # the row-downsampled intermediate buffer
+    c, d, _ = scene.render(small, 3)
+    cam = small.camera()
+    for div, interp in ((4, True), (16, False)):
+        ref = oracle.synthesize_imb(c, d, cam["fx"], cam["ipd"], cam["near"], cam["far"], div, interp)
+        syn = yoro.Synthesizer(**cam, imbuffer_div=div, interpolate=interp)
+        out, mask = syn(torch.from_numpy(c).to(DEV), torch.from_numpy(d).to(DEV))
+        st = syn.status()
+        assert st == 0, f"imbuffer {div} {interp}: status {yoro.STATUS.get(st, st)}"
+        _same((out.cpu().numpy(), mask.cpu().numpy()), ref, f"imbuffer {div} {interp}")
+        syn.close()
 
     frames = []
     for i, (w, h) in enumerate(((1024, 1024), (1440, 1600), (333, 71), (1832, 1920))):

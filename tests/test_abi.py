@@ -97,6 +97,15 @@ def test_create_ex_rejects_bad_options_without_touching_the_device(lib):
         assert lib.yoro_last_create_error() == 1
 
 
+def test_create_imb_rejects_bad_buffer_arguments_without_touching_the_device(lib):
+    import paper_2506_15183_gb300 as yoro
+
+    opt = yoro._Options(3, 0)
+    for div, interp in ((0, 0), (3, 0), (32, 0), (-2, 0), (2, 2), (4, -1)):
+        assert lib.yoro_create_imb(64, 64, 32.0, 32.0, 32.0, 32.0, 0.06, 0.05, 1000.0, opt, div, interp) is None
+        assert lib.yoro_last_create_error() == 1
+
+
 def test_server_rejects_bad_arguments_without_touching_the_device(lib):
     from paper_2506_15183_gb300 import server
 

@@ -2,7 +2,8 @@
 
 Each mutant is a copy of ``oracle/yoro_oracle.c`` with one plausible mistake (a
 dropped term, a wrong sign, index or order), built into a temporary library and
-loaded by a fresh pytest run of ``test_oracle_pins.py``.  That run must fail: if it
+loaded by a fresh pytest run of ``test_oracle_pins.py`` (or, for the intermediate
+buffer's steps, ``test_oracle_imbuffer.py``).  That run must fail: if it
 passed, the pins would not tie the oracle to the paper at that point.
 """
 import os
@@ -21,7 +22,8 @@ MUTANTS = {
     "disparity_sign": ("float t = ((float)x + 0.5f) - disp;", "float t = ((float)x + 0.5f) + disp;"),
     "round_not_floor": ("float f = floorf(t);", "float f = rintf(t);"),
     "trunc_not_floor": ("float f = floorf(t);", "float f = truncf(t);"),
-    "no_near_clamp": ("float c = fminf(fmaxf(z, near_), far_);", "float c = fminf(z, far_);"),
+    "no_near_clamp": ("float c = fminf(fmaxf(z, near_), far_);\n            float disp = k / c;\n            float t = ((float)x",
+                      "float c = fminf(z, far_);\n            float disp = k / c;\n            float t = ((float)x"),
     "farther_wins": ("if (src[o] < 0 || zc[i] < zt[o]) {", "if (src[o] < 0 || zc[i] > zt[o]) {"),
     "last_writer_wins_ties": ("if (src[o] < 0 || zc[i] < zt[o]) {", "if (src[o] < 0 || zc[i] <= zt[o]) {"),
     "t_from_occluder_edge": ("float t = (float)(R - u) / (float)wd;", "float t = (float)(u - L) / (float)wd;"),
@@ -39,12 +41,26 @@ MUTANTS = {
     "fallback_to_occluder": ("    if (R < w)\n        memcpy(out, warped + 4 * ((size_t)v * (size_t)w + (size_t)R), 4);",
                              "    if (L >= 0)\n        memcpy(out, warped + 4 * ((size_t)v * (size_t)w + (size_t)L), 4);"),
     "alpha_not_filled": ("for (int c = 0; c < 4; ++c) {\n                float r", "for (int c = 0; c < 3; ++c) {\n                float r"),
+    # the row-downsampled intermediate buffer, against its own pins
+    "imb_cell_pixel_not_centre": ("int p = div * i + div / 2;", "int p = div * i;", "test_oracle_imbuffer.py"),
+    "imb_target_cell_rounded": ("float tc = floorf(t / (float)div);", "float tc = rintf(t / (float)div);",
+                                "test_oracle_imbuffer.py"),
+    "imb_farther_cell_wins": ("if (wrow[j] < 0 || c < zrow[j]) {", "if (wrow[j] < 0 || c > zrow[j]) {",
+                              "test_oracle_imbuffer.py"),
+    "imb_place_in_cell_dropped": ("int sx = div * wrow[j] + (x - div * j);", "int sx = div * wrow[j];",
+                                  "test_oracle_imbuffer.py"),
+    "imb_neighbour_side_swapped": ("int nb = off < 0.0f ? j - 1 : j + 1;", "int nb = off < 0.0f ? j + 1 : j - 1;",
+                                   "test_oracle_imbuffer.py"),
+    "imb_shift_not_interpolated": ("D = drow[j] + (drow[nb] - drow[j]) * a;", "D = drow[j];",
+                                   "test_oracle_imbuffer.py"),
+    "imb_nearest_texel": ("float v = c0 + (c1 - c0) * f;", "float v = c0;", "test_oracle_imbuffer.py"),
 }
 
 
 @pytest.mark.parametrize("name", sorted(MUTANTS))
 def test_pins_catch_mutant(name, tmp_path):
-    old, new = MUTANTS[name]
+    old, new = MUTANTS[name][:2]
+    pins = MUTANTS[name][2] if len(MUTANTS[name]) > 2 else "test_oracle_pins.py"
     src = open(SRC).read()
     assert src.count(old) == 1, f"mutation site for {name} not found exactly once"
     mut_c = tmp_path / "mutant.c"
@@ -53,6 +69,6 @@ def test_pins_catch_mutant(name, tmp_path):
     subprocess.check_call(["gcc", *oracle.CFLAGS, "-shared", "-fPIC", "-o", str(lib), str(mut_c), "-lm"])
     env = dict(os.environ, YORO_ORACLE_LIB=str(lib))
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
-                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                        os.path.join(ROOT, "tests", pins)],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"mutant {name} passed every pin:\n{r.stdout[-2000:]}"
