@@ -127,7 +127,7 @@ yoro_status run_imb(yoro_ctx* c, const FrameArgs& f, cudaStream_t s)
         }
     }
     const yoro::ImbArgs a = yoro::imb_args(c->d_imb, c->w, c->h, c->imb_div, c->imb_interp);
-    return yoro::imb_launch(f, a, s) == cudaSuccess ? YORO_OK : YORO_ECUDA;
+    return yoro::imb_launch(f, a, c->lim, c->fused_ok, s) == cudaSuccess ? YORO_OK : YORO_ECUDA;
 }
 
 bool uses_imb(const yoro_ctx* c) { return c->imb_div > 1 || c->imb_interp; }

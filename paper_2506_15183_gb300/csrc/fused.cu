@@ -467,6 +467,10 @@ __device__ __forceinline__ void resolve_window(const FrameArgs& f, const float* 
 // (ra = y0-1 or 0, rb = y1 or h-1).  Ends with a barrier, so the next band may reuse
 // shared memory.
 template <int NT, bool VAR>
+__device__ __forceinline__ void fill_band(const FrameArgs& f, int y0, int y1, const Window& s, int* ctr,
+                                          int* rowinfo);
+
+template <int NT, bool VAR>
 __device__ __forceinline__ void run_band(const FrameArgs& f, int y0, int y1, Window s, int* ctr, int* rowinfo)
 {
     constexpr int NW = NT / 32;
@@ -503,6 +507,22 @@ __device__ __forceinline__ void run_band(const FrameArgs& f, int y0, int y1, Win
     // pixels and hole mask leave
     resolve_window<NT>(f, depth, color, nr, y0, y1, s);
     __syncthreads();
+
+    fill_band<NT, VAR>(f, y0, y1, s, ctr, rowinfo);
+}
+
+// P3 of one band [y0, y1) whose window (s.ra set) holds the reached pixels' depths and
+// colors and every window row's reached bitmask.  Writes the band rows' holes to
+// f.out (reached pixels and masks are not touched).  Ends with a barrier.
+template <int NT, bool VAR>
+__device__ __forceinline__ void fill_band(const FrameArgs& f, int y0, int y1, const Window& s, int* ctr,
+                                          int* rowinfo)
+{
+    constexpr int NW = NT / 32;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int w = f.w, h = f.h;
+    const int nwords = s.nwords;
+    const KernelShape<VAR> ks(f);
 
     // ---- P3a: per band row (one warp per row; rows with every pixel reached are done):
     // its last reached column, the border holes right of it, and per 32-pixel word the
@@ -688,6 +708,45 @@ __global__ void __launch_bounds__(NT, MINB) fused_batch(const __grid_constant__ 
     }
 }
 
+// P3 alone over an image that is already resolved in global memory: the reached pixels'
+// colors in f.out, their depths in zt, the hole mask in f.mask (the row-downsampled
+// intermediate buffer's full-resolution image).  Each band's window is loaded (the
+// reached bitmasks by ballot over the mask bytes, depths and colors of the reached
+// pixels), then filled exactly as the fused kernel fills its bands.
+template <int NT>
+__global__ void __launch_bounds__(NT, 1) fill_only(FrameArgs f, const float* __restrict__ zt, int wpad)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    constexpr int NW = NT / 32;
+    int *ctr, *rowinfo;
+    const KernelShape<true> ks(f);
+    Window s = window_layout(smem_raw, f.band + 2 * ks.halo, wpad, f.w, ctr, rowinfo);
+    const int w = f.w, h = f.h, nwords = s.nwords;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nbands = (h + f.band - 1) / f.band;
+    for (int b = blockIdx.x; b < nbands; b += gridDim.x) {
+        const int y0 = b * f.band, y1 = min(y0 + f.band, h);
+        const int ra = max(y0 - ks.halo, 0), rb = min(y1 - 1 + ks.halo, h - 1);
+        const int nr = rb - ra + 1;
+        s.ra = ra;
+        for (int it = warp; it < nr * nwords; it += NW) {
+            const int j = it / nwords, g = it - j * nwords;
+            const int x = (g << 5) + lane;
+            const size_t o = (size_t)(ra + j) * w + x;
+            const bool reached = x < w && f.mask[o] == 0;
+            const uint32_t m = __ballot_sync(0xffffffffu, reached);
+            if (lane == 0 && YORO_BOUND(j < s.slots, kBadHoles)) s.bits[j * nwords + g] = m;
+            if (reached && YORO_BOUND(j * wpad + x < s.slots * wpad, kBadHoles)) {
+                s.zt[j * wpad + x] = __float_as_uint(zt[o]);
+                s.rgba[j * wpad + x] = f.out[o];
+            }
+        }
+        if (threadIdx.x == 0) *ctr = 0;
+        __syncthreads();
+        fill_band<NT, true>(f, y0, y1, s, ctr, rowinfo);
+    }
+}
+
 // Two shapes: 1024 threads with one CTA per SM (large bands), or 512 threads with
 // two CTAs per SM (bands small enough that two fit in shared memory).
 constexpr int kBig = 1024;
@@ -753,7 +812,8 @@ cudaError_t fused_configure(int device, FusedLimits* lim)
     lim->max_width = wmax;
     const void* fns[] = {(const void*)fused_single<kBig, 1, false>, (const void*)fused_single<kSmall, 2, false>,
                          (const void*)fused_single<kBig, 1, true>,  (const void*)fused_single<kSmall, 2, true>,
-                         (const void*)fused_batch<kBig, 1>,         (const void*)fused_batch<kSmall, 2>};
+                         (const void*)fused_batch<kBig, 1>,         (const void*)fused_batch<kSmall, 2>,
+                         (const void*)fill_only<kBig>};
     for (const void* fn : fns) {
         e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
         if (e != cudaSuccess) return e;
@@ -828,5 +888,19 @@ cudaError_t fused_launch_batch(const BatchArgs& a, int wmax, const FusedLimits& 
 }
 
 int fused_max_band(const FusedLimits& lim, int w, int halo) { return max_band(lim, fused_wpad(w), halo); }
+
+cudaError_t fill_only_launch(FrameArgs f, const float* zt, const FusedLimits& lim, cudaStream_t stream)
+{
+    const int wpad = fused_wpad(f.w);
+    // bands as tall as shared memory allows, but at least one per SM
+    const int per_sm = (f.h + lim.sms - 1) / lim.sms;
+    f.band = max(1, min(max_band(lim, wpad, f.halo), per_sm));
+    const size_t smem = fused_smem_bytes(wpad, f.band, f.halo);
+    const int nbands = (f.h + f.band - 1) / f.band;
+    const int grid = nbands < lim.sms ? nbands : lim.sms;
+    if (grid < 1) return cudaSuccess;
+    fill_only<kBig><<<grid, kBig, smem, stream>>>(f, zt, wpad);
+    return cudaGetLastError();
+}
 
 }  // namespace yoro

@@ -25,9 +25,11 @@
 // so the result equals the oracle's byte for byte.
 //
 // Three launches on the caller's stream after clearing the cell keys: cells (one
-// thread per cell), sample (one thread per pixel), fill (one thread per pixel, the
-// hole pixels do the work).  The cell keys and the full-resolution depths live in
-// handle-owned scratch memory.
+// thread per cell), sample (one thread per pixel), and the fill: the fused kernel's
+// band fill over the sampled image (fill_only in fused.cu: a window per band loaded
+// into shared memory, the holes dealt to the warps) when a band fits shared memory,
+// otherwise one thread per pixel from global memory.  The cell keys and the
+// full-resolution depths live in handle-owned scratch memory.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -197,7 +199,8 @@ ImbArgs imb_args(void* scratch, int w, int h, int div, int interp)
     return a;
 }
 
-cudaError_t imb_launch(const FrameArgs& f, const ImbArgs& a, cudaStream_t stream)
+cudaError_t imb_launch(const FrameArgs& f, const ImbArgs& a, const FusedLimits& lim, bool band_fill,
+                       cudaStream_t stream)
 {
     const size_t nc = (size_t)a.ws * f.h, n = (size_t)f.w * f.h;
     if (n == 0) return cudaSuccess;
@@ -208,6 +211,7 @@ cudaError_t imb_launch(const FrameArgs& f, const ImbArgs& a, cudaStream_t stream
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     imb_sample_kernel<<<blocks_for(n, threads), threads, 0, stream>>>(f, a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (band_fill) return fill_only_launch(f, a.zt, lim, stream);
     imb_fill_kernel<<<blocks_for(n, threads), threads, 0, stream>>>(f, a);
     return cudaGetLastError();
 }

@@ -98,7 +98,13 @@ struct ImbArgs {
 };
 size_t imb_scratch_bytes(int w, int h, int div);
 ImbArgs imb_args(void* scratch, int w, int h, int div, int interp);
-cudaError_t imb_launch(const FrameArgs& f, const ImbArgs& a, cudaStream_t stream);
+// band_fill: the frame's band window fits shared memory (fused_ok), so the holes are
+// filled by fill_only_launch; otherwise by one thread per pixel from global memory.
+cudaError_t imb_launch(const FrameArgs& f, const ImbArgs& a, const FusedLimits& lim, bool band_fill,
+                       cudaStream_t stream);
+// The fused kernel's hole fill (P3) over a frame resolved in global memory: reached
+// colors in f.out, their depths in zt, the hole mask in f.mask.
+cudaError_t fill_only_launch(FrameArgs f, const float* zt, const FusedLimits& lim, cudaStream_t stream);
 unsigned imb_status_take();
 
 }  // namespace yoro
