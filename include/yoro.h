@@ -117,10 +117,11 @@ yoro_handle yoro_create_ex(int w, int h, float fx, float fy, float cx, float cy,
  *   resolution (the handle's kernel variant) from the reached pixels, whose depth is
  *   their winning cell's.
  * s = 1 without interpolation is the base path.  Every synthesize call of the handle
- * (fused, unfused, host, mapped) takes this path when s > 1 or interpolate = 1: three
- * launches around handle-owned scratch memory (8 ceil(w/s) h + 4 w h bytes, allocated
- * on the first call).  Returns NULL with YORO_EINVAL for another s or interpolate, and
- * as yoro_create_ex() otherwise.
+ * (fused, unfused, host, mapped) takes this path when s > 1 or interpolate = 1: one
+ * band kernel when a band of rows with its cells fits shared memory, else (and for
+ * yoro_synthesize_unfused) three launches around handle-owned scratch memory
+ * (8 ceil(w/s) h + 4 w h bytes, allocated on the first such call); same result.  Returns NULL with YORO_EINVAL for another s or
+ * interpolate, and as yoro_create_ex() otherwise.
  */
 yoro_handle yoro_create_imb(int w, int h, float fx, float fy, float cx, float cy, float ipd, float near_,
                             float far_, const yoro_options* opt, int imbuffer_div, int interpolate);

@@ -117,8 +117,12 @@ yoro_status run_unfused(yoro_ctx* c, const FrameArgs& f, cudaStream_t s)
 }
 
 // The handle's frames through the row-downsampled intermediate buffer.
-yoro_status run_imb(yoro_ctx* c, const FrameArgs& f, cudaStream_t s)
+// banded: one band kernel when a band's window and cell keys fit (the handle's fused
+// calls); otherwise, and for the unfused call, the separate kernels.
+yoro_status run_imb(yoro_ctx* c, const FrameArgs& f, cudaStream_t s, bool banded)
 {
+    if (banded && c->fused_ok && yoro::imb_band_max(c->lim, c->w, c->halo, c->imb_div) >= 1)
+        return yoro::imb_band_launch(f, c->imb_div, c->imb_interp, c->lim, s) == cudaSuccess ? YORO_OK : YORO_ECUDA;
     if (!c->d_imb) {
         if (cudaMalloc(&c->d_imb, yoro::imb_scratch_bytes(c->w, c->h, c->imb_div)) != cudaSuccess) {
             c->d_imb = nullptr;
@@ -134,7 +138,7 @@ bool uses_imb(const yoro_ctx* c) { return c->imb_div > 1 || c->imb_interp; }
 
 yoro_status run_frame(yoro_ctx* c, FrameArgs f, cudaStream_t s)
 {
-    if (uses_imb(c)) return run_imb(c, f, s);
+    if (uses_imb(c)) return run_imb(c, f, s, true);
     if (!c->fused_ok) return run_unfused(c, f, s);
     f.band = c->shape.band;
     return yoro::fused_launch(f, c->lim, c->shape.two_per_sm, s) == cudaSuccess ? YORO_OK : YORO_ECUDA;
@@ -250,7 +254,7 @@ yoro_status yoro_synthesize_unfused(yoro_handle c, const void* color, const floa
     st = make_frame(c->w, c->h, c->k, c->near_, c->far_, color, depth, out_color, out_mask, &f);
     if (st != YORO_OK) return st;
     apply_options(c, &f);
-    if (uses_imb(c)) return run_imb(c, f, (cudaStream_t)stream);
+    if (uses_imb(c)) return run_imb(c, f, (cudaStream_t)stream, false);
     return run_unfused(c, f, (cudaStream_t)stream);
 }
 

@@ -747,6 +747,132 @@ __global__ void __launch_bounds__(NT, 1) fill_only(FrameArgs f, const float* __r
     }
 }
 
+// The row-downsampled intermediate buffer in one kernel: per band, the window rows'
+// cells are reprojected into 64-bit cell keys in shared memory (after the window),
+// every window pixel is sampled from its cell's winner into the window (depth, color,
+// reached bitmask; the band rows' reached pixels and masks leave for global memory),
+// and the band's holes are filled as the fused kernel fills them.  The steps and their
+// rounding are those of imbuffer.cu's separate kernels (the reading is stated there).
+template <int NT>
+__global__ void __launch_bounds__(NT, 1) imb_band(FrameArgs f, int div, int interp, int wpad, int cells_off)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    constexpr int NW = NT / 32;
+    int *ctr, *rowinfo;
+    const KernelShape<true> ks(f);
+    const int slots = f.band + 2 * ks.halo;
+    Window s = window_layout(smem_raw, slots, wpad, f.w, ctr, rowinfo);
+    const int w = f.w, h = f.h, nwords = s.nwords, ws = (w + div - 1) / div;
+    unsigned long long* cells = reinterpret_cast<unsigned long long*>(smem_raw + cells_off);  // after the window
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t near_m1 = __float_as_uint(f.near_) - 1u, far_m1 = __float_as_uint(f.far_) - 1u;
+    const float inv_s = 1.0f / (float)div;
+    const int lg = __ffs(div) - 1;  // div is a power of two
+    const int nbands = (h + f.band - 1) / f.band;
+    for (int b = blockIdx.x; b < nbands; b += gridDim.x) {
+        const int y0 = b * f.band, y1 = min(y0 + f.band, h);
+        const int ra = max(y0 - ks.halo, 0), rb = min(y1 - 1 + ks.halo, h - 1);
+        const int nr = rb - ra + 1;
+        s.ra = ra;
+        if (f.bulk && lane == 0) {  // one depth row, then its color row, per warp
+            for (int j = warp; j < nr; j += NW) {
+                prefetch_l2(f.depth + (size_t)(ra + j) * w, (uint32_t)w * 4u);
+                prefetch_l2(f.color + (size_t)(ra + j) * w, (uint32_t)w * 4u);
+            }
+        }
+        for (int i = threadIdx.x; i < nr * ws; i += NT) cells[i] = kEmptyKey;
+        if (threadIdx.x == 0) *ctr = 0;
+        __syncthreads();
+        // cells: Alg. 1 on each cell's pixel, Alg. 2 by a 64-bit minimum of the key;
+        // (row j, cell i) of flat index c advance without a division per cell
+        const int dj = NT / ws, di = NT - dj * ws;
+        int cj = (int)threadIdx.x / ws, ci = (int)threadIdx.x - cj * ws;
+        for (int c = threadIdx.x; c < nr * ws; c += NT) {
+            const int j = cj, i = ci;
+            cj += dj;
+            ci += di;
+            if (ci >= ws) {
+                ci -= ws;
+                ++cj;
+            }
+            const int p = min(div * i + (div >> 1), w - 1);
+            const uint32_t zb = clamped_depth_bits(__ldg(f.depth + (size_t)(ra + j) * w + p), near_m1, far_m1);
+            const float disp = __fdiv_rn(f.k, __uint_as_float(zb));
+            const float t = __fsub_rn(__fadd_rn((float)p, 0.5f), disp);
+            const float tc = floorf(__fmul_rn(t, inv_s));
+            if (tc >= 0.0f && tc < (float)ws && YORO_BOUND(c < slots * ws, kBadScatter))
+                atomicMin(&cells[j * ws + (int)tc], zkey(zb, i));
+        }
+        __syncthreads();
+        if (interp) {  // the winner's shift once per cell: its key's low word becomes disp
+            for (int c = threadIdx.x; c < nr * ws; c += NT) {
+                const unsigned long long key = cells[c];
+                if (key != kEmptyKey) {
+                    const uint32_t zb = (uint32_t)(key >> 32);
+                    cells[c] = ((unsigned long long)zb << 32) | __float_as_uint(__fdiv_rn(f.k, __uint_as_float(zb)));
+                }
+            }
+            __syncthreads();
+        }
+        // sampling: each window pixel from its cell's winner; warp per 32-pixel word
+        for (int it = warp; it < nr * nwords; it += NW) {
+            const int j = it / nwords, g = it - j * nwords;
+            const int x = (g << 5) + lane;
+            const int y = ra + j;
+            const unsigned long long* krow = cells + j * ws;
+            const uint32_t* crow = f.color + (size_t)y * w;
+            unsigned long long key = kEmptyKey;
+            if (x < w) key = krow[x >> lg];
+            const bool reached = key != kEmptyKey;
+            const uint32_t m = __ballot_sync(0xffffffffu, reached);
+            if (lane == 0 && YORO_BOUND(j < slots, kBadResolve)) s.bits[j * nwords + g] = m;
+            const bool band = y >= y0 && y < y1;
+            if (band && x < w) f.mask[(size_t)y * w + x] = reached ? 0 : 1;
+            if (!reached) continue;
+            const uint32_t zb = (uint32_t)(key >> 32);
+            const int cj = x >> lg;
+            uint32_t col;
+            if (!interp) {
+                col = __ldg(crow + min(div * (int)(uint32_t)key + (x - div * cj), w - 1));
+            } else {
+                const float dj = __uint_as_float((uint32_t)key);  // disp of the winner
+                const float off =
+                    __fsub_rn(__fadd_rn((float)x, 0.5f), __fadd_rn((float)(div * cj), 0.5f * (float)div));
+                const int nb = off < 0.0f ? cj - 1 : cj + 1;
+                float d = dj;
+                if (off != 0.0f && nb >= 0 && nb < ws && krow[nb] != kEmptyKey) {
+                    const float dn = __uint_as_float((uint32_t)krow[nb]);
+                    d = __fadd_rn(dj, __fmul_rn(__fsub_rn(dn, dj), __fmul_rn(fabsf(off), inv_s)));
+                }
+                const float u = __fadd_rn((float)x, d);
+                if (u <= 0.0f) {
+                    col = __ldg(crow);
+                } else if (u >= (float)(w - 1)) {
+                    col = __ldg(crow + w - 1);
+                } else {
+                    const float fl = floorf(u);
+                    const int i0 = (int)fl;
+                    const float fr = __fsub_rn(u, fl);
+                    const uint32_t c0 = __ldg(crow + i0), c1 = __ldg(crow + i0 + 1);
+                    col = 0u;
+#pragma unroll
+                    for (int ch = 0; ch < 4; ++ch) {
+                        const float v0 = (float)((c0 >> (8 * ch)) & 255u), v1 = (float)((c1 >> (8 * ch)) & 255u);
+                        col |= (uint32_t)rintf(__fadd_rn(v0, __fmul_rn(__fsub_rn(v1, v0), fr))) << (8 * ch);
+                    }
+                }
+            }
+            if (YORO_BOUND(j * wpad + x < slots * wpad, kBadResolve)) {
+                s.zt[j * wpad + x] = zb;
+                s.rgba[j * wpad + x] = col;
+            }
+            if (band) f.out[(size_t)y * w + x] = col;
+        }
+        __syncthreads();
+        fill_band<NT, true>(f, y0, y1, s, ctr, rowinfo);
+    }
+}
+
 // Two shapes: 1024 threads with one CTA per SM (large bands), or 512 threads with
 // two CTAs per SM (bands small enough that two fit in shared memory).
 constexpr int kBig = 1024;
@@ -813,7 +939,7 @@ cudaError_t fused_configure(int device, FusedLimits* lim)
     const void* fns[] = {(const void*)fused_single<kBig, 1, false>, (const void*)fused_single<kSmall, 2, false>,
                          (const void*)fused_single<kBig, 1, true>,  (const void*)fused_single<kSmall, 2, true>,
                          (const void*)fused_batch<kBig, 1>,         (const void*)fused_batch<kSmall, 2>,
-                         (const void*)fill_only<kBig>};
+                         (const void*)fill_only<kBig>,              (const void*)imb_band<kBig>};
     for (const void* fn : fns) {
         e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
         if (e != cudaSuccess) return e;
@@ -888,6 +1014,37 @@ cudaError_t fused_launch_batch(const BatchArgs& a, int wmax, const FusedLimits& 
 }
 
 int fused_max_band(const FusedLimits& lim, int w, int halo) { return max_band(lim, fused_wpad(w), halo); }
+
+static size_t imb_cells_offset(int w, int band, int halo)
+{
+    return (fused_smem_bytes(fused_wpad(w), band, halo) + 15) & ~(size_t)15;
+}
+
+size_t imb_band_smem_bytes(int w, int band, int halo, int div)
+{
+    const int ws = (w + div - 1) / div;
+    return imb_cells_offset(w, band, halo) + (size_t)(band + 2 * halo) * (size_t)ws * sizeof(unsigned long long);
+}
+
+int imb_band_max(const FusedLimits& lim, int w, int halo, int div)
+{
+    int b = 0;
+    while (b < 4096 && imb_band_smem_bytes(w, b + 1, halo, div) <= (size_t)lim.smem_per_block) ++b;
+    return b;
+}
+
+cudaError_t imb_band_launch(FrameArgs f, int div, int interp, const FusedLimits& lim, cudaStream_t stream)
+{
+    const int per_sm = (f.h + lim.sms - 1) / lim.sms;
+    f.band = max(1, min(imb_band_max(lim, f.w, f.halo, div), per_sm));
+    const size_t smem = imb_band_smem_bytes(f.w, f.band, f.halo, div);
+    const int nbands = (f.h + f.band - 1) / f.band;
+    const int grid = nbands < lim.sms ? nbands : lim.sms;
+    if (grid < 1) return cudaSuccess;
+    imb_band<kBig><<<grid, kBig, smem, stream>>>(f, div, interp, fused_wpad(f.w),
+                                                 (int)imb_cells_offset(f.w, f.band, f.halo));
+    return cudaGetLastError();
+}
 
 cudaError_t fill_only_launch(FrameArgs f, const float* zt, const FusedLimits& lim, cudaStream_t stream)
 {

@@ -24,12 +24,14 @@
 // Every float operation is an explicit round-to-nearest intrinsic, never contracted,
 // so the result equals the oracle's byte for byte.
 //
-// Three launches on the caller's stream after clearing the cell keys: cells (one
-// thread per cell), sample (one thread per pixel), and the fill: the fused kernel's
-// band fill over the sampled image (fill_only in fused.cu: a window per band loaded
-// into shared memory, the holes dealt to the warps) when a band fits shared memory,
-// otherwise one thread per pixel from global memory.  The cell keys and the
-// full-resolution depths live in handle-owned scratch memory.
+// When a band's window and its cells' keys fit shared memory the whole path is one
+// band kernel (imb_band in fused.cu: cells, sampling and the fused kernel's band fill
+// in shared memory).  Otherwise three launches on the caller's stream after clearing
+// the cell keys: cells (one thread per cell), sample (one thread per pixel), and the
+// fill: the band fill over the sampled image (fill_only in fused.cu) when a band of
+// the window alone fits, else one thread per pixel from global memory.  The cell keys
+// and the full-resolution depths of the separate kernels live in handle-owned scratch
+// memory.
 #include <cuda_runtime.h>
 
 #include <cstdint>

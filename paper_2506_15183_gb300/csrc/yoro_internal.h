@@ -105,6 +105,11 @@ cudaError_t imb_launch(const FrameArgs& f, const ImbArgs& a, const FusedLimits& 
 // The fused kernel's hole fill (P3) over a frame resolved in global memory: reached
 // colors in f.out, their depths in zt, the hole mask in f.mask.
 cudaError_t fill_only_launch(FrameArgs f, const float* zt, const FusedLimits& lim, cudaStream_t stream);
+// The intermediate buffer in one band kernel (cell keys, sampling and fill in shared
+// memory): the tallest band whose window and cell keys fit (0 if none), and the launch.
+size_t imb_band_smem_bytes(int w, int band, int halo, int div);
+int imb_band_max(const FusedLimits& lim, int w, int halo, int div);
+cudaError_t imb_band_launch(FrameArgs f, int div, int interp, const FusedLimits& lim, cudaStream_t stream);
 unsigned imb_status_take();
 
 }  // namespace yoro

@@ -56,6 +56,7 @@ def test_small_scenes(yoro, div, interp):
         c, d, _ = scene.render(cfg, seed)
         ref = _ref(c, d, cam, div, interp)
         _same(_run(yoro, c, d, cam, div, interp), ref, f"seed {seed} div {div} interp {interp}")
+        # the separate kernels (cells, sampling, band fill over the sampled image)
         _same(_run(yoro, c, d, cam, div, interp, unfused=True), ref, f"unfused call, seed {seed}")
 
 
@@ -95,3 +96,17 @@ def test_ragged_widths_and_extreme_cameras(yoro, w):
         for div, interp in ((2, True), (16, False), (8, True)):
             _same(_run(yoro, c, d, cam, div, interp), _ref(c, d, cam, div, interp),
                   f"w {w} fx {fx} ipd {ipd} div {div} interp {interp}")
+
+
+def test_frame_too_wide_for_a_band(yoro):
+    """Wider than any band window: the separate kernels with the per-pixel fill."""
+    w, h = 9984, 5
+    assert w > yoro.yoro_max_fused_width()
+    rng = np.random.default_rng(99)
+    d = np.repeat(rng.uniform(0.05, 6.0, (h, w // 8)).astype(np.float32), 8, axis=1)
+    c = rng.integers(0, 256, (h, w, 4), dtype=np.uint8)
+    cam = dict(w=w, h=h, fx=w / 2.0, fy=w / 2.0, cx=w / 2.0, cy=h / 2.0, ipd=0.063, near=0.05, far=1000.0)
+    for div, interp in ((4, True), (2, False)):
+        ref = _ref(c, d, cam, div, interp)
+        _same(_run(yoro, c, d, cam, div, interp), ref, f"wide div {div}")
+        _same(_run(yoro, c, d, cam, div, interp, unfused=True), ref, f"wide unfused div {div}")
