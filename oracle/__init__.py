@@ -58,6 +58,8 @@ def _load():
         lib.oracle_synthesize_ex.restype = I
         lib.oracle_synthesize_imb.argtypes = [I, I, F, F, F, F, P, P, I, I, I, I, P, P]
         lib.oracle_synthesize_imb.restype = I
+        lib.oracle_synthesize_pose.argtypes = [I, I, F, F, F, F, P, P, F, F, P, P, I, I, P, P]
+        lib.oracle_synthesize_pose.restype = I
         _lib = lib
     return _lib
 
@@ -157,6 +159,27 @@ def synthesize_imb(color, depth, fx, ipd, near, far, div, interp, kernel_rows=3,
                                        out.ctypes.data, mask.ctypes.data)
     if rc != 0:
         raise RuntimeError(f"oracle_synthesize_imb failed ({rc})")
+    return out, mask
+
+
+def synthesize_pose(color, depth, fx, fy, cx, cy, rot, c, near, far, kernel_rows=3, nearest_first=False):
+    """The path with a general second-eye pose (Eq. 5 with a general M): rotation rot
+    (3x3, p' = rot (p - c)) and position c (3) of the second eye in left-eye camera
+    coordinates; pixels may leave their row."""
+    color = _c(color, np.uint8)
+    depth = _c(depth, np.float32)
+    rot = _c(rot, np.float32).reshape(9)
+    c = _c(c, np.float32).reshape(3)
+    h, w = depth.shape
+    if color.shape != (h, w, 4):
+        raise ValueError("color must be uint8[H,W,4] matching depth")
+    out = np.empty((h, w, 4), np.uint8)
+    mask = np.empty((h, w), np.uint8)
+    rc = _load().oracle_synthesize_pose(w, h, fx, fy, cx, cy, rot.ctypes.data, c.ctypes.data, near, far,
+                                        color.ctypes.data, depth.ctypes.data, int(kernel_rows),
+                                        int(bool(nearest_first)), out.ctypes.data, mask.ctypes.data)
+    if rc != 0:
+        raise RuntimeError(f"oracle_synthesize_pose failed ({rc})")
     return out, mask
 
 

@@ -467,3 +467,97 @@ done:
     free(warped);
     return rc;
 }
+
+/*
+ * General reprojection (Eq. 5 with a general M = (VP_left)^-1 VP_right): the second eye
+ * may be rotated and offset in any direction, so a pixel can leave its row.  Reading:
+ * both eyes share the pinhole intrinsics (fx, fy, cx, cy); the second eye sits at
+ * position c (left-eye camera coordinates) with rotation rot (row-major 3x3, mapping
+ * left-eye camera axes to the second eye's: p' = rot (p - c)).
+ *
+ *   1. Per source pixel (y, x): zc = clamp(depth) as in oracle_disparity (Alg. 1);
+ *      P = ((x + 0.5 - cx) zc / fx, (y + 0.5 - cy) zc / fy, zc);
+ *      P' = rot (P - c), each row as ((r0 q0 + r1 q1) + r2 q2);
+ *      dropped unless P'.z > 0; target (floor(fx P'.x / P'.z + cx),
+ *      floor(fy P'.y / P'.z + cy)), dropped outside the frame.
+ *   2. Alg. 2 per target pixel over the whole frame: the nearest P'.z kept, the lower
+ *      source index y w + x on equal depth (the first of a row-major scan).
+ *   3. Gather the winner's color; its P'.z is the target's depth.
+ *   4. Holes along each row and the Patcher (oracle_hole_edges, oracle_fill_ex), the
+ *      candidates' depths being the targets' P'.z.
+ *
+ * With rot = I and c = (ipd, 0, 0) the target row is y and the column is the base
+ * path's up to rounding; for dyadic parameters (powers of two for fx and the depths,
+ * integers for cx) every step is exact and the result equals oracle_synthesize_ex's.
+ * Returns 0, -1 on bad arguments, -2 if a temporary could not be allocated.
+ */
+int oracle_synthesize_pose(int w, int h, float fx, float fy, float cx, float cy, const float* rot, const float* c,
+                           float near_, float far_, const uint8_t* color, const float* depth, int kernel_rows,
+                           int nearest_first, uint8_t* out_color, uint8_t* mask)
+{
+    if (w < 0 || h < 0 || kernel_rows < 1 || (kernel_rows & 1) == 0) return -1;
+    size_t n = (size_t)w * (size_t)h;
+    if (n == 0) return 0;
+    int64_t* win = (int64_t*)malloc(n * sizeof(int64_t));  /* winner source index, or -1 */
+    float* zt = (float*)malloc(n * sizeof(float));
+    int32_t* src = (int32_t*)malloc(n * sizeof(int32_t));
+    int32_t* L = (int32_t*)malloc(n * sizeof(int32_t));
+    int32_t* R = (int32_t*)malloc(n * sizeof(int32_t));
+    uint8_t* warped = (uint8_t*)malloc(n * 4);
+    int rc = 0;
+    if (!win || !zt || !src || !L || !R || !warped) {
+        rc = -2;
+        goto done;
+    }
+    for (size_t i = 0; i < n; ++i) {
+        win[i] = -1;
+        zt[i] = INFINITY;
+    }
+    /* steps 1 and 2: a row-major scan of the sources */
+    for (int y = 0; y < h; ++y) {
+        for (int x = 0; x < w; ++x) {
+            size_t i = (size_t)y * (size_t)w + (size_t)x;
+            float z = depth[i];
+            if (!(z > 0.0f) || isinf(z)) z = far_;
+            float zc = fminf(fmaxf(z, near_), far_);
+            float px = (((float)x + 0.5f) - cx) * zc / fx;
+            float py = (((float)y + 0.5f) - cy) * zc / fy;
+            float q0 = px - c[0], q1 = py - c[1], q2 = zc - c[2];
+            float X = (rot[0] * q0 + rot[1] * q1) + rot[2] * q2;
+            float Y = (rot[3] * q0 + rot[4] * q1) + rot[5] * q2;
+            float Z = (rot[6] * q0 + rot[7] * q1) + rot[8] * q2;
+            if (!(Z > 0.0f)) continue;
+            float u = floorf(fx * X / Z + cx);
+            float v = floorf(fy * Y / Z + cy);
+            if (!(u >= 0.0f && u < (float)w && v >= 0.0f && v < (float)h)) continue;
+            size_t o = (size_t)v * (size_t)w + (size_t)u;
+            if (win[o] < 0 || Z < zt[o]) {
+                win[o] = (int64_t)i;
+                zt[o] = Z;
+            }
+        }
+    }
+    /* step 3 */
+    for (size_t o = 0; o < n; ++o) {
+        if (win[o] >= 0) {
+            memcpy(warped + 4 * o, color + 4 * (size_t)win[o], 4);
+            src[o] = 0;
+            mask[o] = 0;
+        } else {
+            memset(warped + 4 * o, 0, 4);
+            src[o] = -1;
+            mask[o] = 1;
+        }
+    }
+    /* step 4 */
+    oracle_hole_edges(w, h, src, L, R);
+    oracle_fill_ex(w, h, src, zt, L, R, warped, kernel_rows, nearest_first, out_color);
+done:
+    free(win);
+    free(zt);
+    free(src);
+    free(L);
+    free(R);
+    free(warped);
+    return rc;
+}

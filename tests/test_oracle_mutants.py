@@ -3,7 +3,8 @@
 Each mutant is a copy of ``oracle/yoro_oracle.c`` with one plausible mistake (a
 dropped term, a wrong sign, index or order), built into a temporary library and
 loaded by a fresh pytest run of ``test_oracle_pins.py`` (or, for the intermediate
-buffer's steps, ``test_oracle_imbuffer.py``).  That run must fail: if it
+buffer's and the general reprojection's steps, ``test_oracle_imbuffer.py`` and
+``test_oracle_pose.py``).  That run must fail: if it
 passed, the pins would not tie the oracle to the paper at that point.
 """
 import os
@@ -54,6 +55,14 @@ MUTANTS = {
     "imb_shift_not_interpolated": ("D = drow[j] + (drow[nb] - drow[j]) * a;", "D = drow[j];",
                                    "test_oracle_imbuffer.py"),
     "imb_nearest_texel": ("float v = c0 + (c1 - c0) * f;", "float v = c0;", "test_oracle_imbuffer.py"),
+    # the general reprojection, against its own pins
+    "pose_rotation_transposed": ("float X = (rot[0] * q0 + rot[1] * q1) + rot[2] * q2;",
+                                 "float X = (rot[0] * q0 + rot[3] * q1) + rot[6] * q2;", "test_oracle_pose.py"),
+    "pose_farther_wins": ("if (win[o] < 0 || Z < zt[o]) {", "if (win[o] < 0 || Z > zt[o]) {", "test_oracle_pose.py"),
+    "pose_row_centre_dropped": ("float py = (((float)y + 0.5f) - cy) * zc / fy;", "float py = ((float)y - cy) * zc / fy;",
+                                "test_oracle_pose.py"),
+    "pose_target_rounded": ("float u = floorf(fx * X / Z + cx);", "float u = rintf(fx * X / Z + cx);",
+                            "test_oracle_pose.py"),
 }
 
 
