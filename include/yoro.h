@@ -126,8 +126,28 @@ yoro_handle yoro_create_ex(int w, int h, float fx, float fy, float cx, float cy,
 yoro_handle yoro_create_imb(int w, int h, float fx, float fy, float cx, float cy, float ipd, float near_,
                             float far_, const yoro_options* opt, int imbuffer_div, int interpolate);
 
-/* Status of the last yoro_create() / yoro_create_ex() / yoro_create_imb() on the
- * calling thread (YORO_OK after a success). */
+/*
+ * A context for a general pose of the second eye (Eq. 5 with a general
+ * M = (VP_left)^-1 VP_right): rotated and offset in any direction, so that pixels may
+ * leave their row.  Both eyes share the pinhole intrinsics fx, fy, cx, cy (all used).
+ * rotation: 9 floats, row-major, and position: 3 floats, the second eye's rotation R and
+ * centre c in left-eye camera coordinates: a point p seen by the left eye is at
+ * R (p - c) for the second eye (R = I, c = (ipd, 0, 0) is yoro_create's stereo pair).
+ * Per source pixel: the clamped depth zc (as yoro_create), p = (((x + 0.5) - cx) zc / fx,
+ * ((y + 0.5) - cy) zc / fy, zc), p' = R (p - c) with each component ((r0 q0 + r1 q1) + r2 q2),
+ * dropped unless p'.z > 0, target (floor(fx p'.x / p'.z + cx), floor(fy p'.y / p'.z + cy));
+ * per target the nearest p'.z is kept, the lower source index y w + x on equal depth;
+ * holes are found along the rows and filled by the Patcher (opt: its kernel variant),
+ * with p'.z as the depths.  Every synthesize call of the handle takes this path: three
+ * launches around handle-owned scratch memory (12 w h bytes, allocated on the first
+ * call).  Returns NULL with YORO_EINVAL for NULL or non-finite rotation / position, a
+ * non-positive fy, and as yoro_create_ex() otherwise.
+ */
+yoro_handle yoro_create_pose(int w, int h, float fx, float fy, float cx, float cy, const float* rotation,
+                             const float* position, float near_, float far_, const yoro_options* opt);
+
+/* Status of the last yoro_create*() call on the calling thread (YORO_OK after a
+ * success). */
 yoro_status yoro_last_create_error(void);
 
 /* Release the handle and the device memory it owns.  NULL is accepted.  Pending work

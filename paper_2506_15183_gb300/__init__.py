@@ -21,7 +21,7 @@ __all__ = [
     "yoro_max_fused_width", "yoro_status_string", "yoro_last_create_error", "STATUS",
     "yoro_synthesize_noalloc", "yoro_noalloc_max_pixels", "yoro_tune_batch", "yoro_batch_band",
     "yoro_reset_tuning", "yoro_create_ex", "yoro_synthesize_mapped", "yoro_debug_bounds_enabled",
-    "yoro_debug_selftest", "yoro_create_imb",
+    "yoro_debug_selftest", "yoro_create_imb", "yoro_create_pose",
 ]
 
 _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "libyoro.so")
@@ -70,6 +70,8 @@ def load_library(path: str | None = None, debug: bool = False) -> ctypes.CDLL:
     lib.yoro_create_ex.restype = P
     lib.yoro_create_imb.argtypes = [I, I, F, F, F, F, F, F, F, ctypes.POINTER(_Options), I, I]
     lib.yoro_create_imb.restype = P
+    lib.yoro_create_pose.argtypes = [I, I, F, F, F, F, P, P, F, F, ctypes.POINTER(_Options)]
+    lib.yoro_create_pose.restype = P
     lib.yoro_last_create_error.argtypes = []
     lib.yoro_last_create_error.restype = I
     lib.yoro_destroy.argtypes = [P]
@@ -186,6 +188,27 @@ def yoro_create_imb(w, h, fx, fy, cx, cy, ipd, near, far, kernel_rows=3, nearest
     return _Handle(p, int(w), int(h))
 
 
+def yoro_create_pose(w, h, fx, fy, cx, cy, rotation, position, near, far, kernel_rows=3,
+                     nearest_first=False) -> _Handle:
+    """A context for a general second-eye pose: rotation (3x3, row-major) and position
+    (3) of the second eye in left-eye camera coordinates, p' = rotation (p - position)."""
+    lib = load_library()
+    rot = (ctypes.c_float * 9)(*[float(v) for v in _flat(rotation, 9, "rotation")])
+    pos = (ctypes.c_float * 3)(*[float(v) for v in _flat(position, 3, "position")])
+    opt = _Options(int(kernel_rows), int(bool(nearest_first)))
+    p = lib.yoro_create_pose(int(w), int(h), fx, fy, cx, cy, rot, pos, near, far, ctypes.byref(opt))
+    if not p:
+        raise YoroError(lib.yoro_last_create_error(), "yoro_create_pose")
+    return _Handle(p, int(w), int(h))
+
+
+def _flat(a, n, name):
+    vals = [v for row in a for v in (row if hasattr(row, "__len__") else [row])]
+    if len(vals) != n:
+        raise ValueError(f"{name} must have {n} values")
+    return vals
+
+
 def yoro_destroy(h: _Handle) -> None:
     if h is not None and h.ptr:
         load_library().yoro_destroy(h.ptr)
@@ -300,9 +323,14 @@ class Synthesizer:
     """Owns a handle for one camera; ``__call__`` allocates the outputs with torch."""
 
     def __init__(self, w, h, fx, fy, cx, cy, ipd, near=0.05, far=1000.0, kernel_rows=3, nearest_first=False,
-                 imbuffer_div=1, interpolate=False):
+                 imbuffer_div=1, interpolate=False, pose=None):
+        """pose: None (the stereo pair at +ipd along x) or (rotation 3x3, position 3) of a
+        general second eye, which then replaces ipd."""
         self.w, self.h = int(w), int(h)
-        if imbuffer_div != 1 or interpolate:
+        if pose is not None:
+            self.handle = yoro_create_pose(w, h, fx, fy, cx, cy, pose[0], pose[1], near, far, kernel_rows,
+                                           nearest_first)
+        elif imbuffer_div != 1 or interpolate:
             self.handle = yoro_create_imb(w, h, fx, fy, cx, cy, ipd, near, far, kernel_rows, nearest_first,
                                           imbuffer_div, interpolate)
         elif kernel_rows == 3 and not nearest_first:

@@ -25,12 +25,15 @@ struct yoro_ctx {
     int device;
     int halo, nearest;  // Patcher kernel shape (yoro_options)
     int imb_div, imb_interp;  // row-downsampled intermediate buffer (yoro_create_imb)
+    bool pose;                // general second-eye pose (yoro_create_pose)
+    yoro::PoseArgs pose_args; // its camera and pose (scratch pointers bound per call)
     bool fused_ok;      // the window of one band row fits shared memory
     FusedLimits lim;
     yoro::FusedShape shape;
     unsigned long long* d_zbuf;    // unfused path, h*w keys, allocated on first use
     unsigned char* d_stage;        // host-buffer path, 13*h*w bytes (+ padding), on first use
     void* d_imb;                   // intermediate-buffer path: cell keys and depths, on first use
+    void* d_pose;                  // general-pose path: keys and depths, on first use
 };
 
 namespace {
@@ -136,8 +139,24 @@ yoro_status run_imb(yoro_ctx* c, const FrameArgs& f, cudaStream_t s, bool banded
 
 bool uses_imb(const yoro_ctx* c) { return c->imb_div > 1 || c->imb_interp; }
 
+// The handle's frames with a general second-eye pose.
+yoro_status run_pose(yoro_ctx* c, const FrameArgs& f, cudaStream_t s)
+{
+    if (!c->d_pose) {
+        if (cudaMalloc(&c->d_pose, yoro::pose_scratch_bytes(c->w, c->h)) != cudaSuccess) {
+            c->d_pose = nullptr;
+            cudaGetLastError();
+            return YORO_ENOMEM;
+        }
+    }
+    yoro::PoseArgs p = c->pose_args;
+    yoro::pose_bind_scratch(&p, c->d_pose, c->w, c->h);
+    return yoro::pose_launch(f, p, c->lim, c->fused_ok, s) == cudaSuccess ? YORO_OK : YORO_ECUDA;
+}
+
 yoro_status run_frame(yoro_ctx* c, FrameArgs f, cudaStream_t s)
 {
+    if (c->pose) return run_pose(c, f, s);
     if (uses_imb(c)) return run_imb(c, f, s, true);
     if (!c->fused_ok) return run_unfused(c, f, s);
     f.band = c->shape.band;
@@ -218,6 +237,41 @@ yoro_handle yoro_create_imb(int w, int h, float fx, float fy, float cx, float cy
     return c;
 }
 
+yoro_handle yoro_create_pose(int w, int h, float fx, float fy, float cx, float cy, const float* rotation,
+                             const float* position, float near_, float far_, const yoro_options* opt)
+{
+    if (!rotation || !position) {
+        g_last_create = YORO_EINVAL;
+        return nullptr;
+    }
+    for (int i = 0; i < 9; ++i)
+        if (!std::isfinite(rotation[i])) {
+            g_last_create = YORO_EINVAL;
+            return nullptr;
+        }
+    for (int i = 0; i < 3; ++i)
+        if (!std::isfinite(position[i])) {
+            g_last_create = YORO_EINVAL;
+            return nullptr;
+        }
+    if (!(fy > 0.0f)) {
+        g_last_create = YORO_EINVAL;
+        return nullptr;
+    }
+    yoro_ctx* c = yoro_create_ex(w, h, fx, fy, cx, cy, 0.0f, near_, far_, opt);
+    if (!c) return nullptr;
+    c->pose = true;
+    c->pose_args.fx = fx;
+    c->pose_args.fy = fy;
+    c->pose_args.cx = cx;
+    c->pose_args.cy = cy;
+    for (int i = 0; i < 9; ++i) c->pose_args.rot[i] = rotation[i];
+    for (int i = 0; i < 3; ++i) c->pose_args.c[i] = position[i];
+    c->pose_args.zbuf = nullptr;
+    c->pose_args.zt = nullptr;
+    return c;
+}
+
 yoro_status yoro_last_create_error(void) { return g_last_create; }
 
 void yoro_destroy(yoro_handle c)
@@ -226,6 +280,7 @@ void yoro_destroy(yoro_handle c)
     if (c->d_zbuf) cudaFree(c->d_zbuf);
     if (c->d_stage) cudaFree(c->d_stage);
     if (c->d_imb) cudaFree(c->d_imb);
+    if (c->d_pose) cudaFree(c->d_pose);
     delete c;
 }
 
@@ -254,6 +309,7 @@ yoro_status yoro_synthesize_unfused(yoro_handle c, const void* color, const floa
     st = make_frame(c->w, c->h, c->k, c->near_, c->far_, color, depth, out_color, out_mask, &f);
     if (st != YORO_OK) return st;
     apply_options(c, &f);
+    if (c->pose) return run_pose(c, f, (cudaStream_t)stream);
     if (uses_imb(c)) return run_imb(c, f, (cudaStream_t)stream, false);
     return run_unfused(c, f, (cudaStream_t)stream);
 }
@@ -506,7 +562,8 @@ yoro_status yoro_stream_status(yoro_handle c, void* stream)
     }
     if (cudaPeekAtLastError() != cudaSuccess) return YORO_ECUDA;
     // both words are read (and cleared) whichever is set
-    const unsigned bad = yoro::fused_status_take() | yoro::unfused_status_take() | yoro::imb_status_take();
+    const unsigned bad =
+        yoro::fused_status_take() | yoro::unfused_status_take() | yoro::imb_status_take() | yoro::pose_status_take();
     return bad ? YORO_EDEVICE : YORO_OK;
 }
 

@@ -214,7 +214,16 @@ cudaError_t imb_launch(const FrameArgs& f, const ImbArgs& a, const FusedLimits& 
     imb_sample_kernel<<<blocks_for(n, threads), threads, 0, stream>>>(f, a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (band_fill) return fill_only_launch(f, a.zt, lim, stream);
-    imb_fill_kernel<<<blocks_for(n, threads), threads, 0, stream>>>(f, a);
+    return fill_pixels_launch(f, a.zt, stream);
+}
+
+cudaError_t fill_pixels_launch(const FrameArgs& f, const float* zt, cudaStream_t stream)
+{
+    const size_t n = (size_t)f.w * f.h;
+    if (n == 0) return cudaSuccess;
+    ImbArgs a{};
+    a.zt = const_cast<float*>(zt);  // the fill reads the depths only
+    imb_fill_kernel<<<blocks_for(n, 256), 256, 0, stream>>>(f, a);
     return cudaGetLastError();
 }
 

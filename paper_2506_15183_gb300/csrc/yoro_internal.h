@@ -25,6 +25,7 @@ constexpr unsigned kBadHoles = 4u;     // P3a/P3b: hole bookkeeping or fill inde
 constexpr unsigned kBadUnfused = 8u;   // the z-buffer kernels
 constexpr unsigned kSelfTest = 16u;    // yoro_debug_selftest
 constexpr unsigned kBadImb = 32u;      // row-downsampled intermediate buffer kernels
+constexpr unsigned kBadPose = 64u;     // general-pose reprojection kernels
 
 // One frame as the kernels see it.  color/out are RGBA8 pixels read as uint32.
 struct FrameArgs {
@@ -105,6 +106,24 @@ cudaError_t imb_launch(const FrameArgs& f, const ImbArgs& a, const FusedLimits& 
 // The fused kernel's hole fill (P3) over a frame resolved in global memory: reached
 // colors in f.out, their depths in zt, the hole mask in f.mask.
 cudaError_t fill_only_launch(FrameArgs f, const float* zt, const FusedLimits& lim, cudaStream_t stream);
+// The holes of a frame resolved in global memory (colors in f.out, depths in zt, mask
+// in f.mask), one thread per pixel: for frames too wide for a band window.
+cudaError_t fill_pixels_launch(const FrameArgs& f, const float* zt, cudaStream_t stream);
+
+// General second-eye pose (pose.cu): p' = rot (p - c) with the shared intrinsics.
+struct PoseArgs {
+    float fx, fy, cx, cy;
+    float rot[9];               // row-major
+    float c[3];                 // second eye position in left-eye camera coordinates
+    unsigned long long* zbuf;   // h * w keys (p'.z bits << 32 | source index)
+    float* zt;                  // h * w depths of the reached targets
+};
+size_t pose_scratch_bytes(int w, int h);
+void pose_bind_scratch(PoseArgs* p, void* scratch, int w, int h);
+cudaError_t pose_launch(const FrameArgs& f, const PoseArgs& p, const FusedLimits& lim, bool band_fill,
+                        cudaStream_t stream);
+unsigned pose_status_take();
+
 // The intermediate buffer in one band kernel (cell keys, sampling and fill in shared
 // memory): the tallest band whose window and cell keys fit (0 if none), and the launch.
 size_t imb_band_smem_bytes(int w, int band, int halo, int div);

@@ -3,7 +3,8 @@
 Run by ``test_gpu_debug_bounds.py`` as ``python tests/debug_bounds_check.py``: the
 process loads the debug-bounds library before any other call, synthesizes frames that
 exercise every kernel (fused single-frame launch with the default and variant kernels,
-the batch launch, the unfused launch, the intermediate-buffer launches; tall bands,
+the batch launch, the unfused launch, the intermediate-buffer and general-pose
+launches; tall bands,
 ragged widths, a wide-disparity camera), and checks for each that the status word stayed clear (no range check failed)
 and that the result still equals the CPU oracle byte for byte.  Then the self-test
 kernel must raise ``YORO_EDEVICE`` exactly once.  Prints ``debug-bounds OK`` at the end.
@@ -95,6 +96,25 @@ def main() -> None:
         assert st == 0, f"imbuffer {div} {interp}: status {yoro.STATUS.get(st, st)}"
         _same((out.cpu().numpy(), mask.cpu().numpy()), ref, f"imbuffer {div} {interp}")
         syn.close()
+        # the same frame through the separate kernels
+        syn = yoro.Synthesizer(**cam, imbuffer_div=div, interpolate=interp)
+        out, mask = syn(torch.from_numpy(c).to(DEV), torch.from_numpy(d).to(DEV), unfused=True)
+        st = syn.status()
+        assert st == 0, f"imbuffer unfused {div} {interp}: status {yoro.STATUS.get(st, st)}"
+        _same((out.cpu().numpy(), mask.cpu().numpy()), ref, f"imbuffer unfused {div} {interp}")
+        syn.close()
+
+    # a general second-eye pose (rotated, offset up)
+    rot = np.array([[0.9998, 0.0, 0.02], [0.0, 1.0, 0.0], [-0.02, 0.0, 0.9998]], np.float32)
+    pose = (rot, [0.063, 0.01, 0.0])
+    ref = oracle.synthesize_pose(c, d, cam["fx"], cam["fy"], cam["cx"], cam["cy"], rot, pose[1], cam["near"],
+                                 cam["far"])
+    syn = yoro.Synthesizer(**cam, pose=pose)
+    out, mask = syn(torch.from_numpy(c).to(DEV), torch.from_numpy(d).to(DEV))
+    st = syn.status()
+    assert st == 0, f"pose: status {yoro.STATUS.get(st, st)}"
+    _same((out.cpu().numpy(), mask.cpu().numpy()), ref, "pose")
+    syn.close()
 
     frames = []
     for i, (w, h) in enumerate(((1024, 1024), (1440, 1600), (333, 71), (1832, 1920))):

@@ -106,6 +106,22 @@ def test_create_imb_rejects_bad_buffer_arguments_without_touching_the_device(lib
         assert lib.yoro_last_create_error() == 1
 
 
+def test_create_pose_rejects_bad_arguments_without_touching_the_device(lib):
+    import ctypes
+
+    import paper_2506_15183_gb300 as yoro
+
+    opt = yoro._Options(3, 0)
+    eye = (ctypes.c_float * 9)(1, 0, 0, 0, 1, 0, 0, 0, 1)
+    pos = (ctypes.c_float * 3)(0.063, 0, 0)
+    bad_rot = (ctypes.c_float * 9)(1, 0, 0, 0, float("nan"), 0, 0, 0, 1)
+    bad_pos = (ctypes.c_float * 3)(0.063, float("inf"), 0)
+    for args in ((eye, None), (None, pos), (bad_rot, pos), (eye, bad_pos)):
+        assert lib.yoro_create_pose(64, 64, 32.0, 32.0, 32.0, 32.0, args[0], args[1], 0.05, 1000.0, opt) is None
+        assert lib.yoro_last_create_error() == 1
+    assert lib.yoro_create_pose(64, 64, 32.0, 0.0, 32.0, 32.0, eye, pos, 0.05, 1000.0, opt) is None
+
+
 def test_server_rejects_bad_arguments_without_touching_the_device(lib):
     from paper_2506_15183_gb300 import server
 
