@@ -52,10 +52,11 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (profiling runs)")
     p.add_argument("--serve-seconds", type=float, default=3.0, help="serve workload: paced run length")
-    p.add_argument("--workload", choices=["quest", "batch", "serve", "imbuffer"], default="quest",
+    p.add_argument("--workload", choices=["quest", "batch", "serve", "imbuffer", "pose"], default="quest",
                    help="quest: one 1832x1920 frame per step (the headline); batch: the 64-frame mixed batch; "
                         "serve: 8 headset streams through the serving loop; imbuffer: the 1832x1920 frames "
-                        "through the row-downsampled intermediate buffer")
+                        "through the row-downsampled intermediate buffer; pose: the 1832x1920 frames for a "
+                        "rotated, vertically offset second eye")
     p.add_argument("--imbuffer-div", type=int, default=4, help="imbuffer workload: source pixels per cell")
     p.add_argument("--no-interpolate", action="store_true", help="imbuffer workload: no linear interpolation")
     p.add_argument("--no-tune", action="store_true", help="batch workload: skip the band-height autotuner")
@@ -315,11 +316,25 @@ def run_batch(args):
     }), flush=True)
 
 
-def run_imbuffer(args):
-    """The 1832x1920 workload through the row-downsampled intermediate buffer
-    (yoro_create_imb): the same rotating pool as the headline, one handle per stream (the
-    path uses handle-owned scratch), steps round-robin over the streams.  Algorithmic
-    bytes per pixel: 4 color + 4 / div depth read, 4 color + 1 mask written."""
+# second-eye pose of the pose workload: yaw 0.02 rad, pitch 0.01 rad, at (0.063, 0.005, 0) m
+POSE_YAW, POSE_PITCH, POSE_POS = 0.02, 0.01, (0.063, 0.005, 0.0)
+
+
+def _pose_rotation():
+    cy, sy = np.cos(POSE_YAW), np.sin(POSE_YAW)
+    cp, sp = np.cos(POSE_PITCH), np.sin(POSE_PITCH)
+    ry = np.array([[cy, 0, sy], [0, 1, 0], [-sy, 0, cy]])
+    rx = np.array([[1, 0, 0], [0, cp, -sp], [0, sp, cp]])
+    return (rx @ ry).astype(np.float32)
+
+
+def run_variant(args):
+    """The 1832x1920 workload through a variant path: the row-downsampled intermediate
+    buffer (yoro_create_imb) or a general second-eye pose (yoro_create_pose).  The same
+    rotating pool as the headline, one handle per stream (the paths may use handle-owned
+    scratch), steps round-robin over the streams.  Algorithmic bytes per pixel: 4 color
+    read (+ 4 / div depth for the buffer, + 4 depth for the pose), 4 color + 1 mask
+    written."""
     import torch
 
     import paper_2506_15183_gb300 as yoro
@@ -331,7 +346,12 @@ def run_imbuffer(args):
     div, interp = args.imbuffer_div, not args.no_interpolate
     nstreams = max(1, args.streams)
     streams = [torch.cuda.Stream() for _ in range(nstreams)]
-    handles = [yoro.yoro_create_imb(**cfg.camera(), imbuffer_div=div, interpolate=interp) for _ in streams]
+    cam = cfg.camera()
+    if args.workload == "pose":
+        handles = [yoro.yoro_create_pose(cam["w"], cam["h"], cam["fx"], cam["fy"], cam["cx"], cam["cy"],
+                                         _pose_rotation(), POSE_POS, cam["near"], cam["far"]) for _ in streams]
+    else:
+        handles = [yoro.yoro_create_imb(**cam, imbuffer_div=div, interpolate=interp) for _ in streams]
 
     def step(i):
         f = pool[i % len(pool)]
@@ -361,20 +381,25 @@ def run_imbuffer(args):
             raise yoro.YoroError(status, "kernel status")
         yoro.yoro_destroy(hdl)
     secs = t_ms / 1e3
-    bpp = 4 + 4 / div + 4 + 1
+    pose = args.workload == "pose"
+    bpp = 4 + 4 + 4 + 1 if pose else 4 + 4 / div + 4 + 1
     peak, _ = measured_peaks()
     achieved = bpp * npx * args.steps / secs / 1e9
+    config = ({"workload": "quest 1832x1920, second eye rotated (yaw 0.02, pitch 0.01 rad) at (0.063, 0.005, 0) m",
+               "entry_point": "yoro_synthesize (yoro_create_pose handle)"} if pose else
+              {"workload": "quest 1832x1920 through the intermediate buffer", "imbuffer_div": div,
+               "interpolate": interp, "entry_point": "yoro_synthesize (yoro_create_imb handle)"})
+    config.update(streams=nstreams, pool_frames=len(pool))
     print(json.dumps({
-        "metric": "2nd-eye Mpix/s, intermediate-buffer variant", "value": round(npx * args.steps / secs / 1e6, 3),
+        "metric": "2nd-eye Mpix/s, " + ("general-pose variant" if pose else "intermediate-buffer variant"),
+        "value": round(npx * args.steps / secs / 1e6, 3),
         "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_ms / args.steps, 5),
         "higher_is_better": True, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "quest 1832x1920 through the intermediate buffer", "imbuffer_div": div,
-                   "interpolate": interp, "streams": nstreams, "pool_frames": len(pool),
-                   "entry_point": "yoro_synthesize (yoro_create_imb handle)"},
+        "config": config,
         "frames_per_s": round(args.steps / secs, 1),
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "bytes_per_pixel": bpp},
-        "gpu_launches": 3 * args.steps,
+        "gpu_launches": (3 if pose else 1) * args.steps,  # pose: scatter, gather, fill; buffer: one band kernel
     }), flush=True)
 
 
@@ -512,9 +537,9 @@ def main():
         if rank == 0:
             run_serve(args)
         return
-    if args.workload == "imbuffer":
+    if args.workload in ("imbuffer", "pose"):
         if rank == 0:
-            run_imbuffer(args)
+            run_variant(args)
         return
 
     import torch
