@@ -101,3 +101,27 @@ def test_frame_too_wide_for_a_band(yoro):
     cam = dict(w=w, h=h, fx=w / 2.0, fy=w / 2.0, cx=w / 2.0, cy=h / 2.0, ipd=0.0, near=0.05, far=1000.0)
     pose = POSES[2]
     _same(_run(yoro, c, d, cam, pose), _ref(c, d, cam, pose), "wide")
+
+
+def test_host_and_mapped_entry_points_take_the_variant_paths(yoro):
+    """yoro_synthesize_host and yoro_synthesize_mapped of a pose handle and of an
+    intermediate-buffer handle give the oracle's result too."""
+    cfg = scene.small_config()
+    cam = cfg.camera()
+    c, d, _ = scene.render(cfg, 5)
+    cases = [(yoro.yoro_create_pose(cam["w"], cam["h"], cam["fx"], cam["fy"], cam["cx"], cam["cy"], POSES[3][0],
+                                    POSES[3][1], cam["near"], cam["far"]),
+              _ref(c, d, cam, POSES[3])),
+             (yoro.yoro_create_imb(**cam, imbuffer_div=4, interpolate=True),
+              oracle.synthesize_imb(c, d, cam["fx"], cam["ipd"], cam["near"], cam["far"], 4, True))]
+    for hdl, ref in cases:
+        for fn in (yoro.yoro_synthesize_host, yoro.yoro_synthesize_mapped):
+            hc = torch.from_numpy(c).pin_memory()
+            hd = torch.from_numpy(d).pin_memory()
+            ho = torch.empty((cfg.h, cfg.w, 4), dtype=torch.uint8).pin_memory()
+            hm = torch.empty((cfg.h, cfg.w), dtype=torch.uint8).pin_memory()
+            fn(hdl, hc, hd, ho, hm)
+            torch.cuda.synchronize()
+            assert yoro.yoro_stream_status(hdl) == 0
+            _same((ho.numpy(), hm.numpy()), ref, fn.__name__)
+        yoro.yoro_destroy(hdl)
