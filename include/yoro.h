@@ -120,8 +120,9 @@ yoro_handle yoro_create_ex(int w, int h, float fx, float fy, float cx, float cy,
  * (fused, unfused, host, mapped) takes this path when s > 1 or interpolate = 1: one
  * band kernel when a band of rows with its cells fits shared memory, else (and for
  * yoro_synthesize_unfused) three launches around handle-owned scratch memory
- * (8 ceil(w/s) h + 4 w h bytes, allocated on the first such call); same result.  Returns NULL with YORO_EINVAL for another s or
- * interpolate, and as yoro_create_ex() otherwise.
+ * (8 ceil(w/s) h + 4 w h bytes, allocated on the first such call); same result.
+ * Returns NULL with YORO_EINVAL for another s or interpolate, and as yoro_create_ex()
+ * otherwise.
  */
 yoro_handle yoro_create_imb(int w, int h, float fx, float fy, float cx, float cy, float ipd, float near_,
                             float far_, const yoro_options* opt, int imbuffer_div, int interpolate);
@@ -228,9 +229,11 @@ yoro_status yoro_synthesize_batch(int n, const yoro_frame* frames, void* cuda_st
  */
 yoro_status yoro_tune_batch(int n, const yoro_frame* frames, int reps, void* cuda_stream, int* out_band);
 
-/* Rows per work item that yoro_synthesize_batch uses on the current device for a launch
- * whose widest frame is w pixels: the tuned height, else the tallest that fits shared
- * memory.  0 if w < 1, w > yoro_max_fused_width() or the device cannot be queried. */
+/* Rows per work item that yoro_synthesize_batch uses on the current device for the
+ * widest frame of a launch, w pixels: the tuned height, else the tallest that fits
+ * shared memory.  Narrower frames of the launch take as many rows as fit the same shared
+ * memory with their own row length.  0 if w < 1, w > yoro_max_fused_width() or the
+ * device cannot be queried. */
 int yoro_batch_band(int w);
 
 /* Forget every tuned band height (all devices). */

@@ -436,6 +436,9 @@ yoro_status batch_launch(int n, const yoro_frame* frames, int dev, const FusedLi
             ++cnt;
         }
         const int band = band_override > 0 ? band_override : batch_band(dev, lim, wmax);
+        // the launch's shared memory holds `band` rows of the widest frame; a narrower
+        // frame's window uses its own row stride, so its bands take as many rows as fit
+        const size_t smem = yoro::fused_smem_bytes(yoro::fused_wpad(wmax), band, 1);
         a->n = 0;
         a->total_items = 0;
         a->max_band = band;
@@ -445,7 +448,9 @@ yoro_status batch_launch(int n, const yoro_frame* frames, int dev, const FusedLi
             FrameArgs f;
             make_frame(fr.w, fr.h, fr.fx * fr.ipd, fr.near_, fr.far_, fr.color, fr.depth, fr.out_color,
                        fr.out_hole_mask, &f);
-            f.band = band;
+            int fb = band;
+            while (fb < fr.h && yoro::fused_smem_bytes(yoro::fused_wpad(fr.w), fb + 1, 1) <= smem) ++fb;
+            f.band = fb;
             a->item_start[a->n] = a->total_items;
             a->f[a->n++] = f;
             a->total_items += (f.h + f.band - 1) / f.band;

@@ -702,7 +702,9 @@ __global__ void __launch_bounds__(NT, MINB) fused_batch(const __grid_constant__ 
         }
         const FrameArgs& f = a.f[lo];
         int *ctr, *rowinfo;
-        const Window s = window_layout(smem_raw, a.max_band + 2, wpad, f.w, ctr, rowinfo);
+        // the frame's own row stride: a narrower frame fits more rows (f.band) in the
+        // shared memory sized for max_band rows of the widest
+        const Window s = window_layout(smem_raw, f.band + 2, (f.w + 7) / 8 * 8, f.w, ctr, rowinfo);
         const int y0 = (item - a.item_start[lo]) * f.band;
         run_band<NT, false>(f, y0, min(y0 + f.band, f.h), s, ctr, rowinfo);
     }
