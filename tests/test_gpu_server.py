@@ -114,3 +114,35 @@ def test_admission_follows_the_memory_budget(srv):
     with pytest.raises(y.YoroError):
         s.submit(c, 5)  # no such slot
     s.close()
+
+
+def test_leaving_with_frames_in_flight_completes_them_first(srv):
+    """A stream that leaves while its frames are queued or running: leave() waits for
+    them, frees its slots, and their completions stay available to poll()."""
+    cfg, c, d = _frame(6, 0)
+    cam = cfg.camera()
+    s = srv.Server(1 << 30, max_batch=4)
+    a = s.admit(**cam, slots=3)
+    ref = oracle.synthesize(c, d, cam["fx"], cam["fy"], cam["cx"], cam["cy"], cam["ipd"], cam["near"], cam["far"])
+    for k in range(3):
+        ci, di, _, _ = s.slot(a, k)
+        ci.copy_(torch.from_numpy(c))
+        di.copy_(torch.from_numpy(d))
+    torch.cuda.synchronize()
+    for k in range(3):
+        s.submit(a, k, tag=40 + k)
+    s.leave(a)  # no drain first
+    assert s.memory_used() == 0
+    done = s.poll()
+    assert sorted(r.tag for r in done) == [40, 41, 42] and all(r.status == 0 for r in done)
+    # the server keeps serving: a new stream gets the oracle's bytes
+    b = s.admit(**cam, slots=1)
+    ci, di, co, mo = s.slot(b, 0)
+    ci.copy_(torch.from_numpy(c))
+    di.copy_(torch.from_numpy(d))
+    torch.cuda.synchronize()
+    s.submit(b, 0, tag=50)
+    s.drain()
+    assert [r.tag for r in s.poll()] == [50]
+    assert np.array_equal(co.cpu().numpy(), ref[0]) and np.array_equal(mo.cpu().numpy(), ref[1])
+    s.close()
