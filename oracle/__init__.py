@@ -6,7 +6,8 @@ does not import, link or call anything here, and nothing here imports the produc
 
 Each function mirrors one step of the method (Algorithm 1 closed form, Algorithm 2
 nearest-wins write, the gather, disocclusion edges, Algorithm 3 with Eq. 6); see
-the C source for the definitions and the paper passages they follow.
+the C source for the definitions and the paper passages they follow.  The submodule
+``oracle.unet`` defines the learned hole inpainter (numpy, no C).
 """
 from __future__ import annotations
 

@@ -81,3 +81,35 @@ def test_pins_catch_mutant(name, tmp_path):
                         os.path.join(ROOT, "tests", pins)],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"mutant {name} passed every pin:\n{r.stdout[-2000:]}"
+
+
+UNET = os.path.join(ROOT, "oracle", "unet.py")
+UNET_MUTANTS = {
+    "unet_concat_order": ("a = np.concatenate([skips[l], upsample2(a)], axis=0)",
+                          "a = np.concatenate([upsample2(a), skips[l]], axis=0)"),
+    "unet_bf16_truncates": ("r = ((u + 0x7FFF + lsb) >> 16) << 16", "r = (u >> 16) << 16"),
+    "unet_bf16_ties_up": ("r = ((u + 0x7FFF + lsb) >> 16) << 16", "r = ((u + 0x8000) >> 16) << 16"),
+    "unet_no_bias": ("    return acc + b[:, None, None]\n\n\ndef conv1x1", "    return acc\n\n\ndef conv1x1"),
+    "unet_padding_shifted": ("xp[:, 1:-1, 1:-1] = x", "xp[:, :-2, 1:-1] = x"),
+    "unet_activations_not_rounded": ("return bf16(np.maximum(x, np.float32(0.0)))",
+                                     "return np.maximum(x, np.float32(0.0))"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(UNET_MUTANTS))
+def test_inpainter_pins_catch_mutant(name, tmp_path):
+    """The same for the inpainter's definition (oracle/unet.py): a copy of the oracle
+    package with one mistake comes first on the path of a fresh run of its pins."""
+    import shutil
+
+    old, new = UNET_MUTANTS[name]
+    src = open(UNET).read()
+    assert src.count(old) == 1, f"mutation site for {name} not found exactly once"
+    shutil.copytree(os.path.join(ROOT, "oracle"), tmp_path / "oracle",
+                    ignore=shutil.ignore_patterns("*.so", "__pycache__"))
+    (tmp_path / "oracle" / "unet.py").write_text(src.replace(old, new))
+    env = dict(os.environ, PYTHONPATH=f"{tmp_path}{os.pathsep}{ROOT}")
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        os.path.join(ROOT, "tests", "test_oracle_unet.py")],
+                       cwd=str(tmp_path), env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode != 0, f"mutant {name} passed every pin:\n{r.stdout[-2000:]}"
