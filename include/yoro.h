@@ -275,9 +275,10 @@ yoro_status yoro_debug_selftest(void* cuda_stream);
  * layout as yoro_synthesize(); same result.
  * The z-buffer is one array in the library's device memory, 2^22 keys (32 MiB), held by
  * every GPU that loads the library until the process exits: frames with w * h greater
- * than yoro_noalloc_max_pixels() are rejected with YORO_ETOOBIG.  The first call on a
- * device looks up that array's device address (cudaGetSymbolAddress, no allocation);
- * make that first call before any stream capture.  Every call clears the part of the
+ * than yoro_noalloc_max_pixels() are rejected with YORO_ETOOBIG.  Every call looks up
+ * that array's device address (cudaGetSymbolAddress, no allocation), so the address
+ * stays right after a cudaDeviceReset(); the first call on a device also loads the
+ * library's module there, so make that first call before any stream capture.  Every call clears the part of the
  * array it uses on cuda_stream, and every call on every stream shares the array, so
  * calls that could overlap on the GPU race: serialise them (one stream, or events).
  */

@@ -20,49 +20,80 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "yoro_oracle.c")
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_MT_LIB_PATH = os.path.join(_HERE, "liboracle_mt.so")
 # binary32 semantics: no contraction of a*b+c into an FMA, no fast-math reassociation.
 CFLAGS = ["-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fexcess-precision=standard"]
 _lib = None
+_mt_lib = None
+
+
+def _compile(path: str, extra) -> str:
+    if not os.path.exists(path) or os.path.getmtime(path) < os.path.getmtime(_SRC):
+        tmp = path + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", *CFLAGS, *extra, "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, path)
+    return path
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle into ``oracle/liboracle.so``."""
-    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
-        tmp = _LIB_PATH + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", *CFLAGS, "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _LIB_PATH)
-    return _LIB_PATH
+    """Compile the oracle into ``oracle/liboracle.so`` (one thread) and the all-core
+    build ``oracle/liboracle_mt.so`` (the same source with -fopenmp: independent rows
+    split over the host's cores; the CPU baseline's second leg)."""
+    if force:
+        for p in (_LIB_PATH, _MT_LIB_PATH):
+            if os.path.exists(p):
+                os.remove(p)
+    _compile(_MT_LIB_PATH, ["-fopenmp"])
+    return _compile(_LIB_PATH, [])
+
+
+def _declare(lib):
+    P = ctypes.c_void_p
+    I, F = ctypes.c_int, ctypes.c_float
+    lib.oracle_disparity.argtypes = [I, I, F, F, F, F, P, P, P]
+    lib.oracle_disparity.restype = None
+    lib.oracle_forward_warp.argtypes = [I, I, P, P, P, P]
+    lib.oracle_forward_warp.restype = None
+    lib.oracle_resolve.argtypes = [I, I, P, P, P, P]
+    lib.oracle_resolve.restype = None
+    lib.oracle_hole_edges.argtypes = [I, I, P, P, P]
+    lib.oracle_hole_edges.restype = None
+    lib.oracle_fill.argtypes = [I, I, P, P, P, P, P, P]
+    lib.oracle_fill.restype = None
+    lib.oracle_synthesize.argtypes = [I, I, F, F, F, F, F, F, F, P, P, P, P]
+    lib.oracle_synthesize.restype = I
+    lib.oracle_fill_ex.argtypes = [I, I, P, P, P, P, P, I, I, P]
+    lib.oracle_fill_ex.restype = None
+    lib.oracle_synthesize_ex.argtypes = [I, I, F, F, F, F, F, F, F, P, P, I, I, P, P]
+    lib.oracle_synthesize_ex.restype = I
+    lib.oracle_synthesize_imb.argtypes = [I, I, F, F, F, F, P, P, I, I, I, I, P, P]
+    lib.oracle_synthesize_imb.restype = I
+    lib.oracle_synthesize_pose.argtypes = [I, I, F, F, F, F, P, P, F, F, P, P, I, I, P, P]
+    lib.oracle_synthesize_pose.restype = I
+    lib.oracle_threads.argtypes = []
+    lib.oracle_threads.restype = I
+    return lib
 
 
 def _load():
     global _lib
     if _lib is None:
         # YORO_ORACLE_LIB names a separately built copy (used by the mutation test).
-        lib = ctypes.CDLL(os.environ.get("YORO_ORACLE_LIB") or build())
-        P = ctypes.c_void_p
-        I, F = ctypes.c_int, ctypes.c_float
-        lib.oracle_disparity.argtypes = [I, I, F, F, F, F, P, P, P]
-        lib.oracle_disparity.restype = None
-        lib.oracle_forward_warp.argtypes = [I, I, P, P, P, P]
-        lib.oracle_forward_warp.restype = None
-        lib.oracle_resolve.argtypes = [I, I, P, P, P, P]
-        lib.oracle_resolve.restype = None
-        lib.oracle_hole_edges.argtypes = [I, I, P, P, P]
-        lib.oracle_hole_edges.restype = None
-        lib.oracle_fill.argtypes = [I, I, P, P, P, P, P, P]
-        lib.oracle_fill.restype = None
-        lib.oracle_synthesize.argtypes = [I, I, F, F, F, F, F, F, F, P, P, P, P]
-        lib.oracle_synthesize.restype = I
-        lib.oracle_fill_ex.argtypes = [I, I, P, P, P, P, P, I, I, P]
-        lib.oracle_fill_ex.restype = None
-        lib.oracle_synthesize_ex.argtypes = [I, I, F, F, F, F, F, F, F, P, P, I, I, P, P]
-        lib.oracle_synthesize_ex.restype = I
-        lib.oracle_synthesize_imb.argtypes = [I, I, F, F, F, F, P, P, I, I, I, I, P, P]
-        lib.oracle_synthesize_imb.restype = I
-        lib.oracle_synthesize_pose.argtypes = [I, I, F, F, F, F, P, P, F, F, P, P, I, I, P, P]
-        lib.oracle_synthesize_pose.restype = I
-        _lib = lib
+        _lib = _declare(ctypes.CDLL(os.environ.get("YORO_ORACLE_LIB") or build()))
     return _lib
+
+
+def _load_mt():
+    global _mt_lib
+    if _mt_lib is None:
+        build()
+        _mt_lib = _declare(ctypes.CDLL(_MT_LIB_PATH))
+    return _mt_lib
+
+
+def threads(all_cores: bool = False) -> int:
+    """Threads of the one-thread build (1) or of the all-core build."""
+    return int((_load_mt() if all_cores else _load()).oracle_threads())
 
 
 def _c(a, dtype):
@@ -127,8 +158,10 @@ def fill(src, zt, L, R, warped, kernel_rows=3, nearest_first=False):
     return out
 
 
-def synthesize(color, depth, fx, fy, cx, cy, ipd, near, far, kernel_rows=3, nearest_first=False):
-    """Left eye (color uint8[H,W,4], depth float32[H,W]) -> right eye (color, hole mask)."""
+def synthesize(color, depth, fx, fy, cx, cy, ipd, near, far, kernel_rows=3, nearest_first=False,
+               all_cores=False):
+    """Left eye (color uint8[H,W,4], depth float32[H,W]) -> right eye (color, hole mask).
+    all_cores runs the all-core build (same arithmetic, rows split over threads)."""
     color = _c(color, np.uint8)
     depth = _c(depth, np.float32)
     h, w = depth.shape
@@ -136,7 +169,8 @@ def synthesize(color, depth, fx, fy, cx, cy, ipd, near, far, kernel_rows=3, near
         raise ValueError("color must be uint8[H,W,4] matching depth")
     out = np.empty((h, w, 4), np.uint8)
     mask = np.empty((h, w), np.uint8)
-    rc = _load().oracle_synthesize_ex(w, h, fx, fy, cx, cy, ipd, near, far, color.ctypes.data,
+    lib = _load_mt() if all_cores else _load()
+    rc = lib.oracle_synthesize_ex(w, h, fx, fy, cx, cy, ipd, near, far, color.ctypes.data,
                                       depth.ctypes.data, int(kernel_rows), int(bool(nearest_first)),
                                       out.ctypes.data, mask.ctypes.data)
     if rc != 0:

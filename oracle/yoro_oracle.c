@@ -7,7 +7,10 @@
  *
  * Plain, slow and sequential on purpose: every step is the paper's definition
  * written out in the order the paper gives, so it can be checked against the
- * paper by eye.  Compiled with -O2 -ffp-contract=off and no fast-math, so every
+ * paper by eye.  The row loops of the base path carry OpenMP pragmas: the default
+ * build ignores them (one thread); the all-core CPU baseline compiles the same file
+ * with -fopenmp, which only splits independent rows over threads (each row writes
+ * its own outputs and reads earlier steps' arrays), so its results are the same.  Compiled with -O2 -ffp-contract=off and no fast-math, so every
  * float operation below is one IEEE binary32 operation rounded to nearest even.
  *
  * Precision: binary32 throughout.  The method turns floating point into integers
@@ -37,9 +40,23 @@
  */
 #include <math.h>
 #include <stddef.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+
+/* Threads the row loops run on: 1 in the default build, the OpenMP team size in the
+ * all-core build. */
+int oracle_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
 
 /*
  * Algorithm 1 (Reprojector stage 1) in closed form, per source pixel (y, x).
@@ -65,6 +82,7 @@ void oracle_disparity(int w, int h, float fx, float ipd, float near_, float far_
                       const float* depth, int32_t* xt, float* zc)
 {
     const float k = fx * ipd;
+#pragma omp parallel for schedule(static)
     for (int y = 0; y < h; ++y) {
         for (int x = 0; x < w; ++x) {
             size_t i = (size_t)y * (size_t)w + (size_t)x;
@@ -97,6 +115,7 @@ void oracle_disparity(int w, int h, float fx, float ipd, float near_, float far_
  */
 void oracle_forward_warp(int w, int h, const int32_t* xt, const float* zc, int32_t* src, float* zt)
 {
+#pragma omp parallel for schedule(static)
     for (int y = 0; y < h; ++y) {
         for (int u = 0; u < w; ++u) {
             size_t i = (size_t)y * (size_t)w + (size_t)u;
@@ -125,6 +144,7 @@ void oracle_forward_warp(int w, int h, const int32_t* xt, const float* zc, int32
 void oracle_resolve(int w, int h, const uint8_t* color, const int32_t* src, uint8_t* out_color,
                     uint8_t* mask)
 {
+#pragma omp parallel for schedule(static)
     for (int y = 0; y < h; ++y) {
         for (int u = 0; u < w; ++u) {
             size_t i = (size_t)y * (size_t)w + (size_t)u;
@@ -149,6 +169,7 @@ void oracle_resolve(int w, int h, const uint8_t* color, const int32_t* src, uint
  */
 void oracle_hole_edges(int w, int h, const int32_t* src, int32_t* L, int32_t* R)
 {
+#pragma omp parallel for schedule(dynamic, 8)
     for (int y = 0; y < h; ++y) {
         const int32_t* s = src + (size_t)y * (size_t)w;
         for (int u = 0; u < w; ++u) {
@@ -180,8 +201,8 @@ void oracle_hole_edges(int w, int h, const int32_t* src, int32_t* L, int32_t* R)
  *            image skipped), and in each row the w + 1 columns from
  *            min(R + w, w_img - 1) down to R: the background side, farthest column
  *            first, as Algorithm 3's kernel runs from r.x - r.z up to r.x in the
- *            paper's frame.  Variants (Sec. Patcher: "height of h, h = 3 by
- *            default"): kernel_rows = h gives rows v - (h-1)/2 .. v + (h-1)/2, and
+ *            paper's frame.  Variants (Sec. Patcher: the kernel height is a
+ *            parameter, 3 by default): kernel_rows = h gives rows v - (h-1)/2 .. v + (h-1)/2, and
  *            nearest_first visits each row's columns from R up instead.
  *   A candidate is skipped if it is a hole (it carries no color) or if it is
  *   strictly nearer than d_occ (a foreground pixel, observation O2).  Otherwise:
@@ -253,6 +274,7 @@ static void fill_one(int w, int h, int v, int u, int L, int R, const int32_t* sr
 void oracle_fill_ex(int w, int h, const int32_t* src, const float* zt, const int32_t* L, const int32_t* R,
                     const uint8_t* warped, int kernel_rows, int nearest_first, uint8_t* out_color)
 {
+#pragma omp parallel for schedule(dynamic, 4)
     for (int v = 0; v < h; ++v) {
         for (int u = 0; u < w; ++u) {
             size_t i = (size_t)v * (size_t)w + (size_t)u;
@@ -324,11 +346,10 @@ int oracle_synthesize(int w, int h, float fx, float fy, float cx, float cy, floa
 /*
  * Strategies (c) and (d) of the Reprojector: the resolution-independent intermediate
  * buffer (ImBuffer) downsampled along the row, and the optional linear interpolation.
- * The paper gives only their intent (the ImBuffer "records the distance the pixel
- * shifts", the full-resolution image "is sampled based on linear interpolation of the
- * distance shifted", and a non-hole pixel takes "the color sampled from the
- * full-resolution rendered image, using the location provided by the ImBuffer"); the
- * reading written out here:
+ * The paper gives only their intent (the buffer keeps how far each pixel moves along
+ * its row, the full-resolution image is sampled at a linearly interpolated shift, and a
+ * reached pixel takes its color from the rendered image at the position the buffer
+ * gives); the reading written out here:
  *
  *   s = div in {1, 2, 4, 8, 16} (1/2 .. 1/16 of the per-eye resolution, along the row:
  *   the warp moves pixels along rows only, O1, so rows stay at full resolution).

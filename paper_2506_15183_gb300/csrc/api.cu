@@ -170,6 +170,11 @@ bool camera_valid(int w, int h, float fx, float fy, float cx, float cy, float ip
 {
     return camera_ok(w, h, fx, fy, cx, cy, ipd, near_, far_);
 }
+int checked_frame(int w, int h, float k, float near_, float far_, const void* color, const float* depth, void* out,
+                  unsigned char* mask, FrameArgs* f)
+{
+    return (int)make_frame(w, h, k, near_, far_, color, depth, out, mask, f);
+}
 void set_last_create_error(int st) { g_last_create = (yoro_status)st; }
 }  // namespace yoro
 

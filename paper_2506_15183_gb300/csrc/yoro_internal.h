@@ -79,6 +79,11 @@ cudaError_t fused_launch_batch(const BatchArgs& a, int wmax, const FusedLimits& 
 // api.cu: the camera checks of yoro_create, and the status yoro_last_create_error reports.
 bool camera_valid(int w, int h, float fx, float fy, float cx, float cy, float ipd, float near_, float far_);
 void set_last_create_error(int status);
+// The pointer checks of every device-pointer entry point (null, 4-byte alignment,
+// overlap of outputs with inputs) and the frame description with its disparity
+// decision margin, for the paper's default kernel; returns a yoro_status.
+int checked_frame(int w, int h, float k, float near_, float far_, const void* color, const float* depth, void* out,
+                  unsigned char* mask, FrameArgs* f);
 
 // Status words of the debug-bounds build (0 in release builds): read and cleared,
 // after the caller synchronised.  fused.cu also launches the self-test kernel.

@@ -4,15 +4,14 @@ The no-allocation entry point serves callers that must not call cudaMalloc where
 synthesize a frame (a compositor's per-frame callback, a plugin whose host owns the
 device-memory budget); its z-buffer is an array inside the library that every call
 shares.  Two calls in a row, a large frame then a smaller one, must each equal the
-fused entry point's output byte for byte: the second call must not see what the first
-left in the shared array.  This file is collected last on purpose.
+fused entry point's output and the CPU oracle's byte for byte: the second call must not
+see what the first left in the shared array.  This file is collected last on purpose.
 """
-import ctypes
-
 import numpy as np
 import pytest
 import torch
 
+import oracle
 from paper_2506_15183_gb300 import scene
 
 pytestmark = pytest.mark.gpu
@@ -55,10 +54,16 @@ def test_noalloc_matches_fused_on_two_calls_in_a_row(lib):
                                          mask.data_ptr(), stream)
         assert rc == 0
         torch.cuda.synchronize()
+        got_out, got_mask = out.cpu().numpy(), mask.cpu().numpy()
         ref_out, ref_mask = _fused(cfg, c, d)
-        assert np.array_equal(out.cpu().numpy(), ref_out)
-        assert np.array_equal(mask.cpu().numpy(), ref_mask)
+        assert np.array_equal(got_out, ref_out)
+        assert np.array_equal(got_mask, ref_mask)
         assert ref_mask.any()
+        # and the definition itself
+        or_out, or_mask = oracle.synthesize(c.cpu().numpy(), d.cpu().numpy(), cam["fx"], cam["fy"], cam["cx"],
+                                            cam["cy"], cam["ipd"], cam["near"], cam["far"])
+        assert np.array_equal(got_out, or_out)
+        assert np.array_equal(got_mask, or_mask)
 
 
 def test_noalloc_rejects_frames_beyond_its_array(lib):
