@@ -1,0 +1,67 @@
+/*
+ * yoro_unet.h — C ABI of the learned hole inpainter (part of libyoro.so).
+ *
+ * The paper fills disocclusions with the hand-written Patcher (Sec. Patcher, Alg. 3
+ * with Eq. 6); its learned comparison system is a GAN that this library does not
+ * reproduce.  The inpainter here is an extension of the method: a 4-level U-Net over
+ * 64 x 64 tiles that replaces the Patcher's colors at hole pixels, with the Patcher as
+ * its fallback and its yardstick.  Its definition, written out on the CPU, is
+ * oracle/unet.py:
+ *   input    6 channels per pixel: warped color / 255 (zero at holes), the hole mask,
+ *            near / warped depth (zero at holes), near / source-eye depth;
+ *   encoder  levels of 32, 64, 128, 256 channels, two 3x3 convolutions (zero padding)
+ *            with ReLU each, 2x2 max pooling between levels;
+ *   decoder  nearest 2x upsampling, concatenated after the encoder level's output
+ *            (skip channels first), two 3x3 convolutions with ReLU;
+ *   output   a 1x1 convolution to 3 channels and a logistic sigmoid.
+ * Weights and activations are bfloat16, sums FP32.  The tensor-core kernels sum in
+ * another order than the definition, so their results agree with it within the FP32
+ * error bound of the sums (then one bfloat16 step where a value sits on a rounding
+ * boundary), not bit for bit.
+ *
+ * Layouts: activations are NHWC bfloat16 (T tiles x H x W x C); weights of a 3x3 layer
+ * are K-major bfloat16, Cout rows of 9 * Cin values, k = (3 dy + dx) * Cin + ci.
+ * All pointers are device pointers owned by the caller; work is enqueued on the
+ * caller's stream (a cudaStream_t as void*).
+ */
+#ifndef YORO_UNET_H
+#define YORO_UNET_H
+
+#include "yoro.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/*
+ * One 3x3 convolution layer on the tensor cores: y = ReLU(conv3x3(x, w) + bias) (relu
+ * = 1) or without ReLU (relu = 0), rounded to bfloat16.
+ *   x        T x H x W x Cin bfloat16, Cin a multiple of 32 (pad unused channels with 0)
+ *   wk       Cout x (9 Cin) bfloat16, K-major as above
+ *   bias     Cout floats
+ *   y        output NHWC bfloat16 with y_cstride channels per pixel; the layer writes
+ *            channels y_coff .. y_coff + Cout - 1 (a decoder's concatenation buffer)
+ *   upsample 0: y has T x H x W pixels; 1: y has T x 2H x 2W pixels and every output
+ *            pixel is written to its 2 x 2 block (nearest upsampling)
+ * Shapes: Cout in {32, 64, 128, 256}; W in {8, 16, 32, 64, 128}; T H W a multiple of
+ * 128; when one tile has fewer than 128 pixels, T a multiple of 128 / (H W).  Others:
+ * YORO_EINVAL.  y_cstride and y_coff multiples of 8.  YORO_ECUDA if the launch fails.
+ * A kernel whose internal wait runs out (it never should) records it for
+ * yoro_unet_status().
+ */
+yoro_status yoro_unet_conv3x3(const void* x, int T, int H, int W, int Cin, const void* wk, const float* bias,
+                              void* y, int Cout, int y_cstride, int y_coff, int upsample, int relu,
+                              void* cuda_stream);
+
+/*
+ * Synchronise cuda_stream and report the inpainter kernels' status: YORO_ECUDA if CUDA
+ * reports an error, YORO_EDEVICE if a kernel gave up an internal wait (the record is
+ * read and cleared), else YORO_OK.
+ */
+yoro_status yoro_unet_status(void* cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* YORO_UNET_H */
