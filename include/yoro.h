@@ -169,6 +169,18 @@ yoro_status yoro_synthesize(yoro_handle h, const void* color_rgba8, const float*
                             void* out_color_rgba8, unsigned char* out_hole_mask, void* cuda_stream);
 
 /*
+ * yoro_synthesize() that also writes the warped depth: out_zt (h*w floats, device,
+ * 4-byte aligned, not overlapping any other buffer) receives, at every reached pixel,
+ * the clamped depth of the source that won it (Alg. 2's stored depth), and 0 at holes.
+ * The learned inpainter (yoro_unet.h) takes it as an input channel.  Only for handles
+ * of yoro_create() (the paper's Patcher, no variant) whose frames take the fused
+ * kernel (w <= yoro_max_fused_width()); YORO_EINVAL otherwise.
+ */
+yoro_status yoro_synthesize_zt(yoro_handle h, const void* color_rgba8, const float* depth_f32,
+                               void* out_color_rgba8, unsigned char* out_hole_mask, float* out_zt,
+                               void* cuda_stream);
+
+/*
  * Same result as yoro_synthesize(), computed by separate kernels around a global
  * z-buffer of h*w 64-bit keys (depth bits << 32 | source column) that the handle
  * allocates on first use and keeps.  Works for any width.  Calls that share a

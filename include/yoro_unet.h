@@ -53,6 +53,43 @@ yoro_status yoro_unet_conv3x3(const void* x, int T, int H, int W, int Cin, const
                               void* y, int Cout, int y_cstride, int y_coff, int upsample, int relu,
                               void* cuda_stream);
 
+typedef struct yoro_unet_ctx* yoro_unet;
+
+/* Number of floats in a parameter array: every layer of the definition in order
+ * (enc0a, enc0b, enc1a, ..., enc3b, dec2a, dec2b, dec1a, dec1b, dec0a, dec0b, out), each as
+ * its weights (Cout x Cin x 3 x 3, or 3 x 32 for the 1x1 output layer, row-major) and
+ * then its Cout biases. */
+long long yoro_unet_param_count(void);
+
+/*
+ * An inpainter on the current device.  params: host floats as above (weights are rounded
+ * to bfloat16 here, biases stay FP32); the handle keeps its own copy.  It owns device
+ * buffers for max(max_tiles, the tiles of a max_w x max_h frame) 64 x 64 tiles (about
+ * 2.9 MB per tile).  NULL if an argument is wrong or an allocation fails.
+ */
+yoro_unet yoro_unet_create(const float* params, long long n_params, int max_tiles, int max_w, int max_h);
+void yoro_unet_destroy(yoro_unet u);
+
+/*
+ * The network on T prepared tiles: x is T x 64 x 64 x 32 bfloat16 (the 6 input channels
+ * of the definition, channels 6..31 zero, 16-byte aligned); rgb receives T x 64 x 64 x 3
+ * floats in [0, 1] (the sigmoid output).  T <= the handle's tile capacity.  Calls on one
+ * handle share its buffers: do not overlap them on the GPU.
+ */
+yoro_status yoro_unet_forward(yoro_unet u, const void* x, int T, float* rgb, void* cuda_stream);
+
+/*
+ * Learned inpainting of one synthesized frame, in place.  rgba (w x h RGBA8) holds the
+ * right eye from yoro_synthesize_zt(); mask, zt: its hole mask and warped depth;
+ * src_depth: the left eye's depth (the source).  Every 64 x 64 tile of the frame that
+ * holds a hole pixel (edge tiles padded with zero inputs outside the frame) goes through
+ * the network, and each hole pixel takes rint(clamp(c, 0, 1) * 255) per color and alpha
+ * 255; reached pixels are not touched.  The tile list is built on the device (nothing
+ * is read back).  YORO_ETOOBIG if the frame exceeds the size the handle was created for.
+ */
+yoro_status yoro_unet_inpaint(yoro_unet u, int w, int h, float near_, void* rgba, const unsigned char* mask,
+                              const float* zt, const float* src_depth, void* cuda_stream);
+
 /*
  * Synchronise cuda_stream and report the inpainter kernels' status: YORO_ECUDA if CUDA
  * reports an error, YORO_EDEVICE if a kernel gave up an internal wait (the record is

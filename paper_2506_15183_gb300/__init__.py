@@ -21,7 +21,7 @@ __all__ = [
     "yoro_max_fused_width", "yoro_status_string", "yoro_last_create_error", "STATUS",
     "yoro_synthesize_noalloc", "yoro_noalloc_max_pixels", "yoro_tune_batch", "yoro_batch_band",
     "yoro_reset_tuning", "yoro_create_ex", "yoro_synthesize_mapped", "yoro_debug_bounds_enabled",
-    "yoro_debug_selftest", "yoro_create_imb", "yoro_create_pose",
+    "yoro_debug_selftest", "yoro_create_imb", "yoro_create_pose", "yoro_synthesize_zt",
 ]
 
 _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "libyoro.so")
@@ -102,6 +102,8 @@ def load_library(path: str | None = None, debug: bool = False) -> ctypes.CDLL:
     lib.yoro_debug_bounds_enabled.restype = I
     lib.yoro_debug_selftest.argtypes = [P]
     lib.yoro_debug_selftest.restype = I
+    lib.yoro_synthesize_zt.argtypes = [P, P, P, P, P, P, P]
+    lib.yoro_synthesize_zt.restype = I
     _lib = lib
     return lib
 
@@ -225,6 +227,13 @@ def yoro_synthesize(h: _Handle, color, depth, out_color, out_mask, stream=None) 
     """Right eye of one frame into out_color/out_mask (device tensors), on `stream`."""
     p = _frame_ptrs(h, color, depth, out_color, out_mask, _dev_ptr)
     _check(load_library().yoro_synthesize(h.ptr, *p, _stream(stream)), "yoro_synthesize")
+
+
+def yoro_synthesize_zt(h: _Handle, color, depth, out_color, out_mask, out_zt, stream=None) -> None:
+    """yoro_synthesize that also writes the warped depth (0 at holes) into out_zt (h, w) float32."""
+    p = _frame_ptrs(h, color, depth, out_color, out_mask, _dev_ptr)
+    z = _dev_ptr(out_zt, torch.float32, (h.h, h.w), "out_zt")
+    _check(load_library().yoro_synthesize_zt(h.ptr, *p, z, _stream(stream)), "yoro_synthesize_zt")
 
 
 def yoro_synthesize_unfused(h: _Handle, color, depth, out_color, out_mask, stream=None) -> None:

@@ -90,6 +90,7 @@ yoro_status make_frame(int w, int h, float k, float near_, float far_, const voi
     f->bulk = (w % 4 == 0) && aligned(color, 16) && aligned(depth, 16) && aligned(out, 16) && aligned(mask, 4);
     f->halo = 1;  // the paper's kernel (h = 3, farthest column first) unless a handle says otherwise
     f->nearest = 0;
+    f->zt_out = nullptr;
     return YORO_OK;
 }
 
@@ -301,6 +302,30 @@ yoro_status yoro_synthesize(yoro_handle c, const void* color, const float* depth
     if (st != YORO_OK) return st;
     apply_options(c, &f);
     return run_frame(c, f, (cudaStream_t)stream);
+}
+
+yoro_status yoro_synthesize_zt(yoro_handle c, const void* color, const float* depth, void* out_color,
+                               unsigned char* out_mask, float* out_zt, void* stream)
+{
+    if (!c) return YORO_EINVAL;
+    if ((size_t)c->w * c->h == 0) return YORO_OK;
+    yoro_status st = on_device(c);
+    if (st != YORO_OK) return st;
+    // the fused kernel with the paper's Patcher only
+    if (c->pose || uses_imb(c) || !c->fused_ok || c->halo != 1 || c->nearest) return YORO_EINVAL;
+    FrameArgs f;
+    st = make_frame(c->w, c->h, c->k, c->near_, c->far_, color, depth, out_color, out_mask, &f);
+    if (st != YORO_OK) return st;
+    const size_t n = (size_t)c->w * c->h;
+    if (!out_zt) return YORO_EINVAL;
+    if ((uintptr_t)out_zt & 3u) return YORO_EALIGN;
+    if (overlaps(out_zt, 4 * n, color, 4 * n) || overlaps(out_zt, 4 * n, depth, 4 * n) ||
+        overlaps(out_zt, 4 * n, out_color, 4 * n) || overlaps(out_zt, 4 * n, out_mask, n))
+        return YORO_EINVAL;
+    f.zt_out = out_zt;
+    f.band = c->shape.band;
+    return yoro::fused_launch(f, c->lim, c->shape.two_per_sm, (cudaStream_t)stream) == cudaSuccess ? YORO_OK
+                                                                                                 : YORO_ECUDA;
 }
 
 yoro_status yoro_synthesize_unfused(yoro_handle c, const void* color, const float* depth, void* out_color,

@@ -367,7 +367,7 @@ __device__ __forceinline__ void scatter_window(const FrameArgs& f, const float* 
 // here; their holes are written in P3.  The loads of a batch are unconditional (a hole
 // or a lane past the row end reads column 0, a batch row past the window reads the
 // last window row), so the batch has no branches around its loads.
-template <int RB, bool FULL, int NWI, int DX>
+template <int RB, bool FULL, int NWI, int DX, bool ZT>
 __device__ __forceinline__ void resolve_batch(const FrameArgs& f, const float* depth, const uint32_t* color,
                                               const Window& s, int g, int j0, int nb, int nr, int jb0, int jb1,
                                               uint32_t near_m1, uint32_t far_m1)
@@ -420,8 +420,9 @@ __device__ __forceinline__ void resolve_batch(const FrameArgs& f, const float* d
             for (int q = 0; q < NWI; ++q) {
                 const bool reached = sc[q][u] >= 0;
                 const uint32_t m = __ballot_sync(0xffffffffu, reached);
+                const uint32_t zbits = clamped_depth_bits(zs[q][u], near_m1, far_m1);
                 if (reached && YORO_BOUND(so + q * DX < nr * wpad, kBadResolve)) {
-                    s.zt[so + q * DX] = clamped_depth_bits(zs[q][u], near_m1, far_m1);
+                    s.zt[so + q * DX] = zbits;
                     s.rgba[so + q * DX] = cs[q][u];
                 }
                 if (lane == 0 && YORO_BOUND(g + q * (DX >> 5) < s.nwords && j < nr, kBadResolve))
@@ -430,6 +431,7 @@ __device__ __forceinline__ void resolve_batch(const FrameArgs& f, const float* d
                 if (band && xin[q] && YORO_BOUND(vo + q * DX < f.h * w, kBadResolve)) {
                     if (reached) f.out[vo + q * DX] = cs[q][u];
                     f.mask[vo + q * DX] = reached ? 0 : 1;
+                    if (ZT) f.zt_out[vo + q * DX] = reached ? __uint_as_float(zbits) : 0.0f;
                 }
             }
         }
@@ -438,7 +440,7 @@ __device__ __forceinline__ void resolve_batch(const FrameArgs& f, const float* d
     }
 }
 
-template <int NT>
+template <int NT, bool ZT>
 __device__ __forceinline__ void resolve_window(const FrameArgs& f, const float* depth, const uint32_t* color,
                                                int nr, int y0, int y1, const Window& s)
 {
@@ -451,13 +453,13 @@ __device__ __forceinline__ void resolve_window(const FrameArgs& f, const float* 
         const bool two = g + NW < s.nwords;  // warp-uniform
         int j0 = 0;
         for (; j0 + RB <= nr; j0 += RB) {
-            if (two) resolve_batch<RB, true, 2, DX>(f, depth, color, s, g, j0, RB, nr, jb0, jb1, near_m1, far_m1);
-            else resolve_batch<RB, true, 1, DX>(f, depth, color, s, g, j0, RB, nr, jb0, jb1, near_m1, far_m1);
+            if (two) resolve_batch<RB, true, 2, DX, ZT>(f, depth, color, s, g, j0, RB, nr, jb0, jb1, near_m1, far_m1);
+            else resolve_batch<RB, true, 1, DX, ZT>(f, depth, color, s, g, j0, RB, nr, jb0, jb1, near_m1, far_m1);
         }
         if (j0 < nr) {
-            if (two) resolve_batch<RB, false, 2, DX>(f, depth, color, s, g, j0, nr - j0, nr, jb0, jb1, near_m1,
+            if (two) resolve_batch<RB, false, 2, DX, ZT>(f, depth, color, s, g, j0, nr - j0, nr, jb0, jb1, near_m1,
                                                      far_m1);
-            else resolve_batch<RB, false, 1, DX>(f, depth, color, s, g, j0, nr - j0, nr, jb0, jb1, near_m1,
+            else resolve_batch<RB, false, 1, DX, ZT>(f, depth, color, s, g, j0, nr - j0, nr, jb0, jb1, near_m1,
                                                      far_m1);
         }
     }
@@ -470,13 +472,12 @@ template <int NT, bool VAR>
 __device__ __forceinline__ void fill_band(const FrameArgs& f, int y0, int y1, const Window& s, int* ctr,
                                           int* rowinfo);
 
-template <int NT, bool VAR>
+template <int NT, bool VAR, bool ZT>
 __device__ __forceinline__ void run_band(const FrameArgs& f, int y0, int y1, Window s, int* ctr, int* rowinfo)
 {
     constexpr int NW = NT / 32;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int w = f.w, h = f.h;
-    const int nwords = s.nwords;
     const KernelShape<VAR> ks(f);
     const int ra = max(y0 - ks.halo, 0), rb = min(y1 - 1 + ks.halo, h - 1);
     const int nr = rb - ra + 1;
@@ -505,7 +506,7 @@ __device__ __forceinline__ void run_band(const FrameArgs& f, int y0, int y1, Win
 
     // ---- P2: resolve, gather depths and colors, reached bitmasks; band rows' reached
     // pixels and hole mask leave
-    resolve_window<NT>(f, depth, color, nr, y0, y1, s);
+    resolve_window<NT, ZT>(f, depth, color, nr, y0, y1, s);
     __syncthreads();
 
     fill_band<NT, VAR>(f, y0, y1, s, ctr, rowinfo);
@@ -676,7 +677,7 @@ __device__ __forceinline__ Window window_layout(unsigned char* smem, int slots, 
     return s;
 }
 
-template <int NT, int MINB, bool VAR>
+template <int NT, int MINB, bool VAR, bool ZT = false>
 __global__ void __launch_bounds__(NT, MINB) fused_single(FrameArgs f, int wpad)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -685,7 +686,7 @@ __global__ void __launch_bounds__(NT, MINB) fused_single(FrameArgs f, int wpad)
     const int nbands = (f.h + f.band - 1) / f.band;
     for (int b = blockIdx.x; b < nbands; b += gridDim.x) {
         const int y0 = b * f.band;
-        run_band<NT, VAR>(f, y0, min(y0 + f.band, f.h), s, ctr, rowinfo);
+        run_band<NT, VAR, ZT>(f, y0, min(y0 + f.band, f.h), s, ctr, rowinfo);
     }
 }
 
@@ -706,7 +707,7 @@ __global__ void __launch_bounds__(NT, MINB) fused_batch(const __grid_constant__ 
         // shared memory sized for max_band rows of the widest
         const Window s = window_layout(smem_raw, f.band + 2, (f.w + 7) / 8 * 8, f.w, ctr, rowinfo);
         const int y0 = (item - a.item_start[lo]) * f.band;
-        run_band<NT, false>(f, y0, min(y0 + f.band, f.h), s, ctr, rowinfo);
+        run_band<NT, false, false>(f, y0, min(y0 + f.band, f.h), s, ctr, rowinfo);
     }
 }
 
@@ -940,6 +941,7 @@ cudaError_t fused_configure(int device, FusedLimits* lim)
     lim->max_width = wmax;
     const void* fns[] = {(const void*)fused_single<kBig, 1, false>, (const void*)fused_single<kSmall, 2, false>,
                          (const void*)fused_single<kBig, 1, true>,  (const void*)fused_single<kSmall, 2, true>,
+                         (const void*)fused_single<kBig, 1, false, true>, (const void*)fused_single<kSmall, 2, false, true>,
                          (const void*)fused_batch<kBig, 1>,         (const void*)fused_batch<kSmall, 2>,
                          (const void*)fill_only<kBig>,              (const void*)imb_band<kBig>};
     for (const void* fn : fns) {
@@ -988,11 +990,14 @@ cudaError_t fused_launch(const FrameArgs& f, const FusedLimits& lim, int two_per
     const int nbands = (f.h + f.band - 1) / f.band;
     const int slots = lim.sms * (two_per_sm ? 2 : 1);
     const int grid = nbands < slots ? nbands : slots;
+    if (f.zt_out && var) return cudaErrorInvalidValue;  // the depth output exists for the default kernel
     if (two_per_sm) {
-        if (var) fused_single<kSmall, 2, true><<<grid, kSmall, smem, stream>>>(f, wpad);
+        if (f.zt_out) fused_single<kSmall, 2, false, true><<<grid, kSmall, smem, stream>>>(f, wpad);
+        else if (var) fused_single<kSmall, 2, true><<<grid, kSmall, smem, stream>>>(f, wpad);
         else fused_single<kSmall, 2, false><<<grid, kSmall, smem, stream>>>(f, wpad);
     } else {
-        if (var) fused_single<kBig, 1, true><<<grid, kBig, smem, stream>>>(f, wpad);
+        if (f.zt_out) fused_single<kBig, 1, false, true><<<grid, kBig, smem, stream>>>(f, wpad);
+        else if (var) fused_single<kBig, 1, true><<<grid, kBig, smem, stream>>>(f, wpad);
         else fused_single<kBig, 1, false><<<grid, kBig, smem, stream>>>(f, wpad);
     }
     return cudaGetLastError();

@@ -21,8 +21,12 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <new>
+#include <vector>
 
 #include "yoro.h"
 #include "yoro_internal.h"
@@ -171,12 +175,14 @@ struct ConvArgs {
     int upsample;         // 1: pixel (yy, xx) goes to (2yy + a, 2xx + b), a, b in {0, 1}
     int relu;
     int ncols;            // tensor-memory columns allocated (a power of two >= Cout, >= 32)
+    const int* count;     // optional: tiles at or after *count are skipped (the tile list's length)
 };
 
 __global__ void __launch_bounds__(128, 1)
     conv3x3_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const ConvArgs a)
 {
     extern __shared__ unsigned char smem_raw[];
+    if (a.count && (int)((blockIdx.x * kTileM) / (a.H * a.W)) >= *a.count) return;  // no such tile (uniform)
     unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                                            ~static_cast<uintptr_t>(1023));
     const int b_bytes = a.Cout * kKc * 2;
@@ -353,7 +359,8 @@ unsigned unet_status_take()
 // whole tiles per 128 pixels, Cout in {32, 64, 128, 256}.  Returns cudaErrorInvalidValue
 // for shapes it does not take.
 cudaError_t unet_conv3x3(const void* x, int T, int H, int W, int Cin, const void* wk, const float* bias, void* y,
-                         int Cout, int y_cstride, int y_coff, int upsample, int relu, cudaStream_t stream)
+                         int Cout, int y_cstride, int y_coff, int upsample, int relu, cudaStream_t stream,
+                         const int* count = nullptr)
 {
     if (T < 1 || H < 1 || W < 1 || Cin < kKc || Cin % kKc || (Cout != 32 && Cout != 64 && Cout != 128 && Cout != 256))
         return cudaErrorInvalidValue;
@@ -402,6 +409,7 @@ cudaError_t unet_conv3x3(const void* x, int T, int H, int W, int Cin, const void
     a.upsample = upsample;
     a.relu = relu;
     a.ncols = Cout < 32 ? 32 : Cout;
+    a.count = count;
     const size_t smem = conv_smem_bytes(Cout);
     static bool configured = false;
     if (!configured) {
@@ -414,7 +422,397 @@ cudaError_t unet_conv3x3(const void* x, int T, int H, int W, int Cin, const void
     return cudaGetLastError();
 }
 
+namespace {
+
+constexpr int kTile = 64;  // inference tile: 64 x 64 pixels
+constexpr int kInCh = 6;   // network input channels (padded to 32 in memory)
+constexpr int kLevels = 4;
+constexpr int kWidths[kLevels] = {32, 64, 128, 256};
+
+// ---- small CUDA-core kernels around the convolutions
+
+// Per 64 x 64 tile of a w x h frame: 1 if it holds a hole pixel (mask == 1).
+__global__ void tile_flags_kernel(const uint8_t* __restrict__ mask, int w, int h, int ntx, int* __restrict__ flags)
+{
+    const int tx = blockIdx.x, ty = blockIdx.y;
+    int any = 0;
+    for (int i = threadIdx.x; i < kTile * kTile; i += blockDim.x) {
+        const int x = tx * kTile + (i & (kTile - 1)), y = ty * kTile + (i >> 6);
+        if (x < w && y < h && mask[(size_t)y * w + x]) any = 1;
+    }
+    any = __syncthreads_or(any);
+    if (threadIdx.x == 0) flags[ty * ntx + tx] = any;
+}
+
+// Ordered list of the flagged tiles (index ty * ntx + tx) and its length, one CTA.
+__global__ void tile_list_kernel(const int* __restrict__ flags, int ntiles, int* __restrict__ list,
+                                 int* __restrict__ count)
+{
+    __shared__ int warp_sums[32];
+    __shared__ int base;
+    if (threadIdx.x == 0) base = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int c0 = 0; c0 < ntiles; c0 += blockDim.x) {
+        const int i = c0 + threadIdx.x;
+        const int f = i < ntiles ? flags[i] : 0;
+        int incl = f;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        if (lane == 31) warp_sums[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            const int nw = blockDim.x >> 5;
+            int ws = lane < nw ? warp_sums[lane] : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, ws, o);
+                if (lane >= o) ws += v;
+            }
+            if (lane < nw) warp_sums[lane] = ws;  // inclusive prefix of warp totals
+        }
+        __syncthreads();
+        const int before = base + (warp ? warp_sums[warp - 1] : 0) + incl - f;
+        if (f) list[before] = i;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) base = before + f;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *count = base;
+}
+
+__device__ __forceinline__ uint16_t bf16_bits(float v)
+{
+    const __nv_bfloat16 b = __float2bfloat16_rn(v);
+    return *reinterpret_cast<const uint16_t*>(&b);
+}
+
+// The network input of listed tile ti, pixel (py, px): the six channels of the
+// definition (warped color / 255 and 0 at holes, the hole mask, near / warped depth and
+// 0 at holes, near / source depth), rounded to bfloat16, then 26 zero channels.  Pixels
+// outside the frame (edge tiles) are all zero.
+__global__ void tile_input_kernel(const uint32_t* __restrict__ rgba, const uint8_t* __restrict__ mask,
+                                  const float* __restrict__ zt, const float* __restrict__ zsrc, int w, int h,
+                                  int ntx, float near_, const int* __restrict__ list, const int* __restrict__ count,
+                                  uint16_t* __restrict__ x)
+{
+    const int ti = blockIdx.y;
+    if (ti >= *count) return;
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;  // pixel of the tile
+    if (p >= kTile * kTile) return;
+    const int tile = list[ti];
+    const int gx = (tile % ntx) * kTile + (p & (kTile - 1)), gy = (tile / ntx) * kTile + (p >> 6);
+    float c[kInCh] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+    if (gx < w && gy < h) {
+        const size_t o = (size_t)gy * w + gx;
+        const bool hole = mask[o] != 0;
+        if (!hole) {
+            const uint32_t v = rgba[o];
+            c[0] = __fdiv_rn((float)(v & 255u), 255.0f);
+            c[1] = __fdiv_rn((float)((v >> 8) & 255u), 255.0f);
+            c[2] = __fdiv_rn((float)((v >> 16) & 255u), 255.0f);
+            c[4] = __fdiv_rn(near_, fmaxf(zt[o], near_));
+        }
+        c[3] = hole ? 1.0f : 0.0f;
+        c[5] = __fdiv_rn(near_, fmaxf(zsrc[o], near_));
+    }
+    uint4 q[4] = {};
+    uint32_t* qw = reinterpret_cast<uint32_t*>(q);
+    qw[0] = (uint32_t)bf16_bits(c[0]) | ((uint32_t)bf16_bits(c[1]) << 16);
+    qw[1] = (uint32_t)bf16_bits(c[2]) | ((uint32_t)bf16_bits(c[3]) << 16);
+    qw[2] = (uint32_t)bf16_bits(c[4]) | ((uint32_t)bf16_bits(c[5]) << 16);
+    uint4* dst = reinterpret_cast<uint4*>(x + ((size_t)ti * kTile * kTile + p) * 32);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) dst[i] = q[i];
+}
+
+// 2x2 max pooling of channels [0, C) of x (T x H x W, cstride channels) into y (T x H/2 x
+// W/2 x C), eight channels per thread.  bfloat16 values compare exactly as floats.
+__global__ void maxpool_kernel(const uint16_t* __restrict__ x, int T, int H, int W, int cstride, int C,
+                               uint16_t* __restrict__ y, const int* __restrict__ count)
+{
+    const int Ho = H / 2, Wo = W / 2, cv = C / 8;
+    const long long total = (long long)T * Ho * Wo * cv;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int v = (int)(i % cv);
+        long long r = i / cv;
+        const int xo = (int)(r % Wo);
+        r /= Wo;
+        const int yo = (int)(r % Ho);
+        const int t = (int)(r / Ho);
+        if (count && t >= *count) continue;
+        float m[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) m[k] = -INFINITY;
+#pragma unroll
+        for (int ab = 0; ab < 4; ++ab) {
+            const size_t px = ((size_t)t * H + 2 * yo + (ab >> 1)) * W + 2 * xo + (ab & 1);
+            const uint4 q = *reinterpret_cast<const uint4*>(x + px * cstride + v * 8);
+            const uint32_t qw[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                m[k] = fmaxf(m[k], __uint_as_float((k & 1 ? qw[k >> 1] & 0xffff0000u : qw[k >> 1] << 16)));
+        }
+        uint4 o;
+        uint32_t* ow = reinterpret_cast<uint32_t*>(&o);
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            ow[k] = (__float_as_uint(m[2 * k]) >> 16) | (__float_as_uint(m[2 * k + 1]) & 0xffff0000u);
+        *reinterpret_cast<uint4*>(y + (((size_t)t * Ho + yo) * Wo + xo) * C + v * 8) = o;
+    }
+}
+
+// The output layer: a 1x1 convolution of the 32 channels (FP32 sums in channel order,
+// then the bias) and the logistic sigmoid 1 / (1 + exp(-z)).  mode 0: the three colors of
+// every pixel of every tile to rgb (T x 64 x 64 x 3 floats).  mode 1: compose into a frame:
+// each hole pixel of a listed tile takes rint(clamp(c, 0, 1) * 255) per color and alpha 255.
+__global__ void output_kernel(const uint16_t* __restrict__ a, const float* __restrict__ wo,
+                              const float* __restrict__ bo, int T, const int* __restrict__ count, int mode,
+                              float* __restrict__ rgb, const int* __restrict__ list, int ntx, int w, int h,
+                              const uint8_t* __restrict__ mask, uint32_t* __restrict__ frame)
+{
+    const int ti = blockIdx.y;
+    if (ti >= T || (count && ti >= *count)) return;
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= kTile * kTile) return;
+    int gx = 0, gy = 0;
+    if (mode == 1) {
+        const int tile = list[ti];
+        gx = (tile % ntx) * kTile + (p & (kTile - 1));
+        gy = (tile / ntx) * kTile + (p >> 6);
+        if (gx >= w || gy >= h || !mask[(size_t)gy * w + gx]) return;
+    }
+    const uint4* src = reinterpret_cast<const uint4*>(a + ((size_t)ti * kTile * kTile + p) * 32);
+    float v[32];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const uint4 q = src[i];
+        const uint32_t qw[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            v[8 * i + 2 * k] = __uint_as_float(qw[k] << 16);
+            v[8 * i + 2 * k + 1] = __uint_as_float(qw[k] & 0xffff0000u);
+        }
+    }
+    float col[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        float acc = 0.0f;
+#pragma unroll
+        for (int ci = 0; ci < 32; ++ci) acc = __fadd_rn(acc, __fmul_rn(wo[c * 32 + ci], v[ci]));
+        const float z = __fadd_rn(acc, bo[c]);
+        col[c] = __fdiv_rn(1.0f, __fadd_rn(1.0f, expf(-z)));
+    }
+    if (mode == 0) {
+        float* o = rgb + ((size_t)ti * kTile * kTile + p) * 3;
+        o[0] = col[0];
+        o[1] = col[1];
+        o[2] = col[2];
+    } else {
+        uint32_t out = 0xff000000u;
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            out |= (uint32_t)rintf(__fmul_rn(fminf(fmaxf(col[c], 0.0f), 1.0f), 255.0f)) << (8 * c);
+        frame[(size_t)gy * w + gx] = out;
+    }
+}
+
+void host_bf16(const float* src, size_t n, uint16_t* dst)
+{
+    for (size_t i = 0; i < n; ++i) {
+        uint32_t u;
+        std::memcpy(&u, &src[i], 4);
+        if ((u & 0x7fffffffu) > 0x7f800000u) {  // NaN stays NaN
+            dst[i] = (uint16_t)((u >> 16) | 0x40u);
+            continue;
+        }
+        u += 0x7fffu + ((u >> 16) & 1u);
+        dst[i] = (uint16_t)(u >> 16);
+    }
+}
+
+}  // namespace
+
+// Parameters of the network: 14 3x3 layers (enc0a, enc0b, ..., enc3b, dec2a, dec2b, dec1a,
+// dec1b, dec0a, dec0b) and the 1x1 output layer, in the order of the definition.
+struct UnetLayer {
+    int cin, cout, cin_pad;
+    uint16_t* wk;  // device, K-major bfloat16
+    float* bias;   // device
+};
+
+struct UnetNet {
+    UnetLayer conv[14];
+    float* wout;  // device: 3 x 32 (bfloat16 values as floats), then 3 biases
+    int max_tiles;
+    // activations, NHWC bfloat16, for max_tiles tiles
+    uint16_t *in0, *e0a, *cat0, *p0, *e1a, *cat1, *p1, *e2a, *cat2, *p2, *e3a, *d2a, *d1a, *d0a, *d0b;
+    int *flags, *list, *count;
+    int max_grid_tiles;  // capacity of flags / list
+};
+
+size_t unet_param_count()
+{
+    size_t n = 0;
+    int cin = kInCh;
+    for (int l = 0; l < kLevels; ++l) {
+        n += (size_t)kWidths[l] * cin * 9 + kWidths[l] + (size_t)kWidths[l] * kWidths[l] * 9 + kWidths[l];
+        cin = kWidths[l];
+    }
+    for (int l = kLevels - 2; l >= 0; --l) {
+        const int c = kWidths[l];
+        n += (size_t)c * (c + kWidths[l + 1]) * 9 + c + (size_t)c * c * 9 + c;
+    }
+    return n + 3 * 32 + 3;
+}
+
+static void layer_dims(int i, int* cin, int* cout)
+{
+    // i = 0..7 encoder (level i / 2), 8..13 decoder (levels 2, 1, 0)
+    if (i < 8) {
+        const int l = i / 2;
+        *cout = kWidths[l];
+        *cin = (i % 2) ? kWidths[l] : (l ? kWidths[l - 1] : kInCh);
+    } else {
+        const int l = 2 - (i - 8) / 2;
+        *cout = kWidths[l];
+        *cin = ((i - 8) % 2) ? kWidths[l] : kWidths[l] + kWidths[l + 1];
+    }
+}
+
+void unet_free(UnetNet* n)
+{
+    if (!n) return;
+    for (auto& L : n->conv) {
+        cudaFree(L.wk);
+        cudaFree(L.bias);
+    }
+    cudaFree(n->wout);
+    uint16_t* bufs[] = {n->in0, n->e0a, n->cat0, n->p0, n->e1a, n->cat1, n->p1, n->e2a,
+                        n->cat2, n->p2, n->e3a, n->d2a, n->d1a, n->d0a, n->d0b};
+    for (uint16_t* b : bufs) cudaFree(b);
+    cudaFree(n->flags);
+    cudaFree(n->list);
+    cudaFree(n->count);
+    delete n;
+}
+
+UnetNet* unet_create(const float* params, size_t n_params, int max_tiles, int max_grid_tiles)
+{
+    if (!params || n_params != unet_param_count() || max_tiles < 1 || max_grid_tiles < 1) return nullptr;
+    UnetNet* n = new UnetNet();
+    std::memset(n, 0, sizeof *n);
+    n->max_tiles = (max_tiles + 1) & ~1;  // even: the 8 x 8 level takes two tiles per 128-pixel MMA tile
+    n->max_grid_tiles = max_grid_tiles;
+    bool ok = true;
+    const float* p = params;
+    std::vector<uint16_t> hk;
+    for (int i = 0; i < 14 && ok; ++i) {
+        int cin, cout;
+        layer_dims(i, &cin, &cout);
+        UnetLayer& L = n->conv[i];
+        L.cin = cin;
+        L.cout = cout;
+        L.cin_pad = (cin + 31) / 32 * 32;
+        // (cout, cin, 3, 3) -> (cout, 3, 3, cin_pad), bfloat16
+        std::vector<float> km((size_t)cout * 9 * L.cin_pad, 0.0f);
+        for (int co = 0; co < cout; ++co)
+            for (int ci = 0; ci < cin; ++ci)
+                for (int t = 0; t < 9; ++t) km[((size_t)co * 9 + t) * L.cin_pad + ci] = p[((size_t)co * cin + ci) * 9 + t];
+        p += (size_t)cout * cin * 9;
+        hk.resize(km.size());
+        host_bf16(km.data(), km.size(), hk.data());
+        ok = cudaMalloc(&L.wk, hk.size() * 2) == cudaSuccess && cudaMalloc(&L.bias, cout * 4) == cudaSuccess &&
+             cudaMemcpy(L.wk, hk.data(), hk.size() * 2, cudaMemcpyHostToDevice) == cudaSuccess &&
+             cudaMemcpy(L.bias, p, cout * 4, cudaMemcpyHostToDevice) == cudaSuccess;
+        p += cout;
+    }
+    if (ok) {  // output layer: bfloat16-rounded weights kept as floats, FP32 biases
+        std::vector<uint16_t> b16(96);
+        host_bf16(p, 96, b16.data());
+        float wo[99];
+        for (int i = 0; i < 96; ++i) {
+            const uint32_t u = (uint32_t)b16[i] << 16;
+            std::memcpy(&wo[i], &u, 4);
+        }
+        for (int i = 0; i < 3; ++i) wo[96 + i] = p[96 + i];
+        ok = cudaMalloc(&n->wout, sizeof wo) == cudaSuccess &&
+             cudaMemcpy(n->wout, wo, sizeof wo, cudaMemcpyHostToDevice) == cudaSuccess;
+    }
+    const size_t T = n->max_tiles, P0 = T * 64 * 64, P1 = T * 32 * 32, P2 = T * 16 * 16, P3 = T * 8 * 8;
+    struct {
+        uint16_t** b;
+        size_t elems;
+    } al[] = {{&n->in0, P0 * 32}, {&n->e0a, P0 * 32}, {&n->cat0, P0 * 96}, {&n->p0, P1 * 32}, {&n->e1a, P1 * 64},
+              {&n->cat1, P1 * 192}, {&n->p1, P2 * 64}, {&n->e2a, P2 * 128}, {&n->cat2, P2 * 384},
+              {&n->p2, P3 * 128}, {&n->e3a, P3 * 256}, {&n->d2a, P2 * 128}, {&n->d1a, P1 * 64},
+              {&n->d0a, P0 * 32}, {&n->d0b, P0 * 32}};
+    for (auto& x : al)
+        if (ok) ok = cudaMalloc(x.b, x.elems * 2) == cudaSuccess;
+    if (ok) {
+        // the in0 buffer of tiles never written stays zero (T rounded up to even)
+        ok = cudaMemset(n->in0, 0, P0 * 32 * 2) == cudaSuccess &&
+             cudaMalloc(&n->flags, (size_t)max_grid_tiles * 4) == cudaSuccess &&
+             cudaMalloc(&n->list, (size_t)max_grid_tiles * 4) == cudaSuccess &&
+             cudaMalloc(&n->count, 4) == cudaSuccess;
+    }
+    if (!ok) {
+        cudaGetLastError();
+        unet_free(n);
+        return nullptr;
+    }
+    return n;
+}
+
+// The 14 convolutions and the pools over the first T tiles of in0 (tiles at or after
+// *count skipped when count is given); the last layer's activations end in d0b.
+cudaError_t unet_run(UnetNet* n, int T, const int* count, cudaStream_t s)
+{
+    const int Te = (T + 1) & ~1;
+    cudaError_t e = cudaSuccess;
+    auto conv = [&](int i, const uint16_t* x, int H, void* y, int cstride, int coff, int up) {
+        if (e != cudaSuccess) return;
+        const UnetLayer& L = n->conv[i];
+        e = unet_conv3x3(x, Te, H, H, L.cin_pad, L.wk, L.bias, y, L.cout, cstride, coff, up, 1, s, count);
+    };
+    auto pool = [&](const uint16_t* x, int H, int cstride, int C, uint16_t* y) {
+        if (e != cudaSuccess) return;
+        const long long total = (long long)Te * (H / 2) * (H / 2) * (C / 8);
+        const int blocks = (int)std::min<long long>((total + 255) / 256, 4096);
+        maxpool_kernel<<<blocks, 256, 0, s>>>(x, Te, H, H, cstride, C, y, count);
+        e = cudaGetLastError();
+    };
+    conv(0, n->in0, 64, n->e0a, 32, 0, 0);     // enc0a
+    conv(1, n->e0a, 64, n->cat0, 96, 0, 0);    // enc0b -> skip of level 0
+    pool(n->cat0, 64, 96, 32, n->p0);
+    conv(2, n->p0, 32, n->e1a, 64, 0, 0);      // enc1a
+    conv(3, n->e1a, 32, n->cat1, 192, 0, 0);   // enc1b -> skip of level 1
+    pool(n->cat1, 32, 192, 64, n->p1);
+    conv(4, n->p1, 16, n->e2a, 128, 0, 0);     // enc2a
+    conv(5, n->e2a, 16, n->cat2, 384, 0, 0);   // enc2b -> skip of level 2
+    pool(n->cat2, 16, 384, 128, n->p2);
+    conv(6, n->p2, 8, n->e3a, 256, 0, 0);      // enc3a
+    conv(7, n->e3a, 8, n->cat2, 384, 128, 1);  // enc3b, upsampled after the level-2 skip
+    conv(8, n->cat2, 16, n->d2a, 128, 0, 0);   // dec2a
+    conv(9, n->d2a, 16, n->cat1, 192, 64, 1);  // dec2b, upsampled after the level-1 skip
+    conv(10, n->cat1, 32, n->d1a, 64, 0, 0);   // dec1a
+    conv(11, n->d1a, 32, n->cat0, 96, 32, 1);  // dec1b, upsampled after the level-0 skip
+    conv(12, n->cat0, 64, n->d0a, 32, 0, 0);   // dec0a
+    conv(13, n->d0a, 64, n->d0b, 32, 0, 0);    // dec0b
+    return e;
+}
+
 }  // namespace yoro
+
+struct yoro_unet_ctx {
+    yoro::UnetNet* net;
+    int device;
+    int max_w, max_h;
+};
 
 extern "C" {
 
@@ -428,6 +826,77 @@ yoro_status yoro_unet_conv3x3(const void* x, int T, int H, int W, int Cin, const
                                              (cudaStream_t)cuda_stream);
     if (e == cudaErrorInvalidValue) return YORO_EINVAL;
     return e == cudaSuccess ? YORO_OK : YORO_ECUDA;
+}
+
+long long yoro_unet_param_count(void) { return (long long)yoro::unet_param_count(); }
+
+yoro_unet yoro_unet_create(const float* params, long long n_params, int max_tiles, int max_w, int max_h)
+{
+    if (!params || n_params <= 0 || max_tiles < 0 || max_w < 0 || max_h < 0 || max_w > 65536 || max_h > 65536)
+        return nullptr;
+    const int grid_tiles = ((max_w + 63) / 64) * ((max_h + 63) / 64);
+    const int tiles = std::max(std::max(max_tiles, grid_tiles), 2);
+    yoro_unet_ctx* c = new (std::nothrow) yoro_unet_ctx();
+    if (!c) return nullptr;
+    if (cudaGetDevice(&c->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return nullptr;
+    }
+    c->max_w = max_w;
+    c->max_h = max_h;
+    c->net = yoro::unet_create(params, (size_t)n_params, tiles, std::max(grid_tiles, 1));
+    if (!c->net) {
+        delete c;
+        return nullptr;
+    }
+    return c;
+}
+
+void yoro_unet_destroy(yoro_unet u)
+{
+    if (!u) return;
+    yoro::unet_free(u->net);
+    delete u;
+}
+
+yoro_status yoro_unet_forward(yoro_unet u, const void* x, int T, float* rgb, void* cuda_stream)
+{
+    if (!u || !x || !rgb || T < 0 || T > u->net->max_tiles) return YORO_EINVAL;
+    if (T == 0) return YORO_OK;
+    if (((uintptr_t)x & 15u) || ((uintptr_t)rgb & 3u)) return YORO_EALIGN;
+    const cudaStream_t s = (cudaStream_t)cuda_stream;
+    if (cudaMemcpyAsync(u->net->in0, x, (size_t)T * 64 * 64 * 32 * 2, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+        return YORO_ECUDA;
+    if (yoro::unet_run(u->net, T, nullptr, s) != cudaSuccess) return YORO_ECUDA;
+    yoro::output_kernel<<<dim3(16, (unsigned)T), 256, 0, s>>>(u->net->d0b, u->net->wout, u->net->wout + 96, T,
+                                                            nullptr, 0, rgb, nullptr, 0, 0, 0, nullptr, nullptr);
+    return cudaGetLastError() == cudaSuccess ? YORO_OK : YORO_ECUDA;
+}
+
+yoro_status yoro_unet_inpaint(yoro_unet u, int w, int h, float near_, void* rgba, const unsigned char* mask,
+                              const float* zt, const float* src_depth, void* cuda_stream)
+{
+    if (!u || w < 0 || h < 0 || !(near_ > 0.0f) || !std::isfinite(near_)) return YORO_EINVAL;
+    if ((size_t)w * h == 0) return YORO_OK;
+    if (w > u->max_w || h > u->max_h) return YORO_ETOOBIG;
+    if (!rgba || !mask || !zt || !src_depth) return YORO_EINVAL;
+    if (((uintptr_t)rgba | (uintptr_t)zt | (uintptr_t)src_depth) & 3u) return YORO_EALIGN;
+    yoro::UnetNet* n = u->net;
+    const cudaStream_t s = (cudaStream_t)cuda_stream;
+    const int ntx = (w + 63) / 64, nty = (h + 63) / 64;
+    yoro::tile_flags_kernel<<<dim3(ntx, nty), 256, 0, s>>>(mask, w, h, ntx, n->flags);
+    yoro::tile_list_kernel<<<1, 1024, 0, s>>>(n->flags, ntx * nty, n->list, n->count);
+    const int T = ntx * nty;  // launches cover every tile; those past the list's length return at once
+    yoro::tile_input_kernel<<<dim3(16, (unsigned)T), 256, 0, s>>>(static_cast<const uint32_t*>(rgba), mask, zt,
+                                                                src_depth, w, h, ntx, near_, n->list, n->count,
+                                                                n->in0);
+    if (cudaGetLastError() != cudaSuccess) return YORO_ECUDA;
+    if (yoro::unet_run(n, T, n->count, s) != cudaSuccess) return YORO_ECUDA;
+    yoro::output_kernel<<<dim3(16, (unsigned)T), 256, 0, s>>>(n->d0b, n->wout, n->wout + 96, T, n->count, 1,
+                                                            nullptr, n->list, ntx, w, h, mask,
+                                                            static_cast<uint32_t*>(rgba));
+    return cudaGetLastError() == cudaSuccess ? YORO_OK : YORO_ECUDA;
 }
 
 yoro_status yoro_unet_status(void* cuda_stream)

@@ -41,6 +41,7 @@ struct FrameArgs {
     int bulk;     // 1: rows are 16-byte aligned (w % 4 == 0), bulk copies + vector stores
     int halo;     // Patcher kernel rows on each side of v: kernel height 2 halo + 1 (default 1)
     int nearest;  // 1: kernel columns nearest first (R up); 0: farthest first (default)
+    float* zt_out;  // optional (fused default kernel only): warped depth per pixel, 0 at holes
 };
 
 // Up to kMaxBatch frames travel in the kernel's parameter space (< 32 KB).

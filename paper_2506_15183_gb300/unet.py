@@ -70,3 +70,78 @@ def conv3x3(x: torch.Tensor, wk: torch.Tensor, bias: torch.Tensor, y: torch.Tens
 
 def status(stream=None) -> int:
     return _lib().yoro_unet_status(_stream(stream))
+
+
+def _lib_net():
+    lib = _lib()
+    if not hasattr(lib, "_net_declared"):
+        P, I, F, L = ctypes.c_void_p, ctypes.c_int, ctypes.c_float, ctypes.c_longlong
+        lib.yoro_unet_param_count.argtypes = []
+        lib.yoro_unet_param_count.restype = L
+        lib.yoro_unet_create.argtypes = [P, L, I, I, I]
+        lib.yoro_unet_create.restype = P
+        lib.yoro_unet_destroy.argtypes = [P]
+        lib.yoro_unet_destroy.restype = None
+        lib.yoro_unet_forward.argtypes = [P, P, I, P, P]
+        lib.yoro_unet_forward.restype = I
+        lib.yoro_unet_inpaint.argtypes = [P, I, I, F, P, P, P, P, P]
+        lib.yoro_unet_inpaint.restype = I
+        lib._net_declared = True
+    return lib
+
+
+def param_count() -> int:
+    return int(_lib_net().yoro_unet_param_count())
+
+
+def flatten_params(p: dict, names) -> np.ndarray:
+    """Parameters as one float32 array in the order of ``names`` (the definition's layer
+    order): each layer's weights, then its biases."""
+    parts = []
+    for name in names:
+        parts += [np.asarray(p[name + ".w"], np.float32).reshape(-1), np.asarray(p[name + ".b"], np.float32)]
+    return np.concatenate(parts)
+
+
+class Inpainter:
+    """yoro_unet_create / destroy, forward and inpaint."""
+
+    def __init__(self, params: np.ndarray, max_tiles: int = 0, max_w: int = 0, max_h: int = 0):
+        params = np.ascontiguousarray(params, np.float32)
+        lib = _lib_net()
+        self.ptr = lib.yoro_unet_create(params.ctypes.data, params.size, int(max_tiles), int(max_w), int(max_h))
+        if not self.ptr:
+            raise RuntimeError("yoro_unet_create failed (parameter count or allocation)")
+
+    def forward(self, x: torch.Tensor, rgb: torch.Tensor, stream=None) -> None:
+        """x (T, 64, 64, 32) bf16 -> rgb (T, 64, 64, 3) float32."""
+        T = x.shape[0]
+        if tuple(x.shape[1:]) != (64, 64, 32):
+            raise ValueError("x must be (T, 64, 64, 32)")
+        if rgb.dtype != torch.float32 or tuple(rgb.shape) != (T, 64, 64, 3) or not rgb.is_cuda:
+            raise ValueError("rgb must be a CUDA float32 tensor (T, 64, 64, 3)")
+        _check(_lib_net().yoro_unet_forward(self.ptr, _bf16_ptr(x, "x"), T, rgb.data_ptr(), _stream(stream)),
+               "yoro_unet_forward")
+
+    def inpaint(self, rgba: torch.Tensor, mask: torch.Tensor, zt: torch.Tensor, src_depth: torch.Tensor,
+                near: float, stream=None) -> None:
+        """In place: hole pixels of rgba (h, w, 4) uint8 take the network's colors."""
+        h, w = mask.shape
+        for t, dt, shp, name in ((rgba, torch.uint8, (h, w, 4), "rgba"), (mask, torch.uint8, (h, w), "mask"),
+                                 (zt, torch.float32, (h, w), "zt"), (src_depth, torch.float32, (h, w), "src_depth")):
+            if not t.is_cuda or t.dtype != dt or tuple(t.shape) != shp or not t.is_contiguous():
+                raise ValueError(f"{name} must be a contiguous CUDA {dt} tensor {shp}")
+        _check(_lib_net().yoro_unet_inpaint(self.ptr, w, h, float(near), rgba.data_ptr(), mask.data_ptr(),
+                                            zt.data_ptr(), src_depth.data_ptr(), _stream(stream)),
+               "yoro_unet_inpaint")
+
+    def close(self) -> None:
+        if self.ptr:
+            _lib_net().yoro_unet_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001 - interpreter shutdown
+            pass

@@ -112,3 +112,164 @@ def test_conv_into_concat_buffer_and_upsampled(un):
 
 def test_conv_without_relu(un):
     _case(un, 1, 16, 16, 64, 64, seed=10, relu=False)
+
+
+# ---- the whole network and the frame path -------------------------------------------
+
+def _frame_tiles(seed, w=256, h=256):
+    """A plain-path frame of a small scene (oracle steps) and its 64x64 tile inputs."""
+    import oracle
+    from paper_2506_15183_gb300 import scene
+
+    cfg = scene.small_config().replace(w=w, h=h)
+    c, d, _ = scene.render(cfg, seed)
+    st = oracle.synthesize_steps(c, d, cfg.fx, cfg.ipd, cfg.near, cfg.far)
+    return cfg, c, d, st
+
+
+def _pad_to_tiles(a, h, w):
+    H, W = (h + 63) // 64 * 64, (w + 63) // 64 * 64
+    out = np.zeros((H, W) + a.shape[2:], a.dtype)
+    out[:h, :w] = a
+    return out
+
+
+def _weights(seed):
+    p = ref.init_weights(seed)
+    rng = np.random.default_rng(seed + 1)
+    for name, _, bs in ref.layer_shapes():
+        p[name + ".b"] = rng.normal(0.0, 0.05, bs).astype(np.float32)
+    return p
+
+
+def _x_gpu(xs):
+    """(T, 6, 64, 64) definition inputs -> (T, 64, 64, 32) bf16 on the GPU."""
+    T = xs.shape[0]
+    x = np.zeros((T, 64, 64, 32), np.float32)
+    x[..., :6] = np.transpose(xs, (0, 2, 3, 1))
+    return _bf16_t(x)
+
+
+def _net(un, p, **kw):
+    names = [n for n, _, _ in ref.layer_shapes()]
+    return un.Inpainter(un.flatten_params(p, names), **kw)
+
+
+def test_forward_matches_definition(un):
+    """The 14 tensor-core layers, pools, upsampled concatenations and the output layer
+    on three tiles of a warped frame (an odd count: the 8 x 8 level pairs tiles).  The
+    layers agree with the definition within their bound (test above); through the
+    network those one-step bfloat16 differences propagate, so the colors are compared
+    with a sanity bound: every color within 0.03, mean within 0.003 (of [0, 1])."""
+    cfg, c, d, st = _frame_tiles(3)
+    hole_tiles = [(ty, tx) for ty in range(4) for tx in range(4)
+                  if st["mask"][64 * ty:64 * ty + 64, 64 * tx:64 * tx + 64].any()][:3]
+    assert len(hole_tiles) == 3
+    xs = np.stack([ref.tile_input(st["warped"][64 * ty:64 * ty + 64, 64 * tx:64 * tx + 64],
+                                  st["mask"][64 * ty:64 * ty + 64, 64 * tx:64 * tx + 64],
+                                  st["zt"][64 * ty:64 * ty + 64, 64 * tx:64 * tx + 64],
+                                  d[64 * ty:64 * ty + 64, 64 * tx:64 * tx + 64], cfg.near)
+                   for ty, tx in hole_tiles])
+    p = _weights(11)
+    net = _net(un, p, max_tiles=4)
+    rgb = torch.zeros((3, 64, 64, 3), dtype=torch.float32, device="cuda")
+    net.forward(_x_gpu(xs), rgb)
+    assert un.status() == 0
+    g = rgb.cpu().numpy()
+    for t in range(3):
+        o = ref.forward(xs[t], p).transpose(1, 2, 0)
+        diff = np.abs(g[t].astype(np.float64) - o)
+        assert diff.max() <= 0.03 and diff.mean() <= 0.003, (t, diff.max(), diff.mean())
+    net.close()
+
+
+def test_every_layer_on_the_definitions_activations(un):
+    """Each layer of a real forward pass, fed the definition's own input for that layer
+    (so no earlier difference propagates), against the definition's output, within the
+    per-layer bound of the tests above: real weights and activations, the skip
+    concatenations and the upsampled stores."""
+    cfg, c, d, st = _frame_tiles(4)
+    ty, tx = next((ty, tx) for ty in range(4) for tx in range(4)
+                  if st["mask"][64 * ty:64 * ty + 64, 64 * tx:64 * tx + 64].any())
+    sl = np.s_[64 * ty:64 * ty + 64, 64 * tx:64 * tx + 64]
+    x = ref.bf16(ref.tile_input(st["warped"][sl], st["mask"][sl], st["zt"][sl], d[sl], cfg.near))
+    p = {k: (ref.bf16(v) if k.endswith(".w") else v) for k, v in _weights(12).items()}
+    layers = []  # (name, input (C, H, W), output (C, H, W))
+    a, skips = x, []
+    for l in range(4):
+        if l:
+            a = ref.maxpool2(a)
+        for s in "ab":
+            o = ref.relu_bf16(ref.conv3x3(a, p[f"enc{l}{s}.w"], p[f"enc{l}{s}.b"]))
+            layers.append((f"enc{l}{s}", a, o))
+            a = o
+        skips.append(a)
+    for l in (2, 1, 0):
+        a = np.concatenate([skips[l], ref.upsample2(a)], axis=0)
+        for s in "ab":
+            o = ref.relu_bf16(ref.conv3x3(a, p[f"dec{l}{s}.w"], p[f"dec{l}{s}.b"]))
+            layers.append((f"dec{l}{s}", a, o))
+            a = o
+    for name, xin, o in layers:
+        cin, H, W = xin.shape
+        cp = un.pad32(cin)
+        xg = np.zeros((2, H, W, cp), np.float32)  # two copies: the 8 x 8 level takes tiles in pairs
+        xg[:, :, :, :cin] = np.transpose(xin, (1, 2, 0))[None]
+        w = p[name + ".w"]
+        cout = w.shape[0]
+        y = torch.zeros((2, H, W, cout), dtype=torch.bfloat16, device="cuda")
+        un.conv3x3(_bf16_t(xg), _bf16_t(un.kmajor(w)), torch.from_numpy(p[name + ".b"]).cuda(), y)
+        assert un.status() == 0
+        absum = ref.conv3x3(np.abs(xin), np.abs(w), np.zeros(cout, np.float32)).astype(np.float64)
+        for t in range(2):
+            _compare(y[t].float().cpu().numpy().transpose(2, 0, 1), o, absum, 9 * cin)
+
+
+@pytest.mark.parametrize("w,h", [(256, 256), (200, 136)])
+def test_inpaint_frame(un, w, h):
+    """The frame path: hole tiles found on the device, edge tiles padded with zero
+    inputs, hole pixels composed from the network's colors, everything else untouched.
+    Against the definition's compose() on the same tiles: reached pixels and hole-free
+    tiles byte for byte; hole pixels within 8 levels, mean within 1 level."""
+    import paper_2506_15183_gb300 as yoro
+
+    cfg, c, d, st = _frame_tiles(5, w, h)
+    syn = yoro.Synthesizer(**cfg.camera())
+    hdl = syn.handle
+    rgba = torch.empty((h, w, 4), dtype=torch.uint8, device="cuda")
+    mask = torch.empty((h, w), dtype=torch.uint8, device="cuda")
+    zt = torch.empty((h, w), dtype=torch.float32, device="cuda")
+    dg = torch.from_numpy(d).cuda()
+    yoro.yoro_synthesize_zt(hdl, torch.from_numpy(c).cuda(), dg, rgba, mask, zt)
+    torch.cuda.synchronize()
+    plain = rgba.cpu().numpy()
+    assert np.array_equal(plain, st["out"]) and np.array_equal(mask.cpu().numpy(), st["mask"])
+    # the warped depth: the winner's clamped depth at reached pixels (Alg. 2's stored depth), 0 at holes
+    assert np.array_equal(zt.cpu().numpy(), np.where(st["mask"].astype(bool), 0.0, st["zt"]).astype(np.float32))
+    p = _weights(13)
+    net = _net(un, p, max_w=w, max_h=h)
+    net.inpaint(rgba, mask, zt, dg, cfg.near)
+    assert un.status() == 0
+    got = rgba.cpu().numpy()
+    # the definition on the zero-padded frame
+    W2, H2 = (w + 63) // 64 * 64, (h + 63) // 64 * 64
+    warped, m, z, ds = (_pad_to_tiles(a, h, w) for a in (st["warped"], st["mask"], st["zt"], d))
+    inside = _pad_to_tiles(np.ones((h, w), bool), h, w)
+    expect = _pad_to_tiles(plain, h, w)
+    for ty in range(H2 // 64):
+        for tx in range(W2 // 64):
+            sl = np.s_[64 * ty:64 * ty + 64, 64 * tx:64 * tx + 64]
+            if not m[sl].any():
+                continue
+            # an edge tile's pixels outside the frame are all-zero inputs (yoro_unet_inpaint)
+            xin = ref.tile_input(warped[sl], m[sl], z[sl], ds[sl], cfg.near) * inside[sl][None]
+            col = ref.forward(xin, p)
+            expect[sl] = ref.compose(expect[sl], m[sl], col)
+    expect = expect[:h, :w]
+    hole = st["mask"].astype(bool)
+    assert np.array_equal(got[~hole], plain[~hole])
+    diff = np.abs(got[hole].astype(int) - expect[hole].astype(int))
+    assert diff.max() <= 8 and diff.mean() <= 1.0, (diff.max(), diff.mean())
+    assert np.all(got[hole][:, 3] == 255)
+    net.close()
+    syn.close()
