@@ -53,11 +53,12 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (profiling runs)")
     p.add_argument("--serve-seconds", type=float, default=3.0, help="serve workload: paced run length")
-    p.add_argument("--workload", choices=["quest", "batch", "serve", "imbuffer", "pose"], default="quest",
+    p.add_argument("--workload", choices=["quest", "batch", "serve", "imbuffer", "pose", "inpaint"], default="quest",
                    help="quest: one 1832x1920 frame per step (the headline); batch: the 64-frame mixed batch; "
                         "serve: 8 headset streams through the serving loop; imbuffer: the 1832x1920 frames "
                         "through the row-downsampled intermediate buffer; pose: the 1832x1920 frames for a "
-                        "rotated, vertically offset second eye")
+                        "rotated, vertically offset second eye; inpaint: the learned inpainter (network on 64x64 "
+                        "tiles and the frame path)")
     p.add_argument("--imbuffer-div", type=int, default=4, help="imbuffer workload: source pixels per cell")
     p.add_argument("--no-interpolate", action="store_true", help="imbuffer workload: no linear interpolation")
     p.add_argument("--no-tune", action="store_true", help="batch workload: skip the band-height autotuner")
@@ -531,6 +532,81 @@ def run_serve(args):
     }), flush=True)
 
 
+def run_inpaint(args):
+    """The learned inpainter: (1) the network alone on every 64x64 tile of a 1832x1920
+    frame (870 tiles per step, inputs resident), timed with CUDA events, against the
+    measured bfloat16 tensor peak; (2) the frame path: yoro_synthesize_zt then
+    yoro_unet_inpaint on the quest frames (rotating pool), frames/s and per-frame latency."""
+    import torch
+
+    import paper_2506_15183_gb300 as yoro
+    from paper_2506_15183_gb300 import scene
+    from paper_2506_15183_gb300 import unet as un
+    from paper_2506_15183_gb300 import weights as W
+
+    cfg = scene.quest_config()
+    if W.exists():
+        params, weights_kind = W.load_flat(), "trained (paper_2506_15183_gb300/weights/unet.yw)"
+    else:
+        params, weights_kind = W.init_params(1), "initial (seeded He-normal)"
+    ntx, nty = (cfg.w + 63) // 64, (cfg.h + 63) // 64
+    T = ntx * nty
+    net = un.Inpainter(params, max_tiles=T, max_w=cfg.w, max_h=cfg.h)
+    g = torch.Generator(device="cuda").manual_seed(5)
+    x = torch.zeros((T, 64, 64, 32), dtype=torch.bfloat16, device="cuda")
+    x[..., :6] = torch.rand((T, 64, 64, 6), generator=g, device="cuda").to(torch.bfloat16)
+    rgb = torch.empty((T, 64, 64, 3), dtype=torch.float32, device="cuda")
+    stream = torch.cuda.Stream()
+    for _ in range(max(3, args.warmup)):
+        net.forward(x, rgb, stream=stream)
+    stream.synchronize()
+    steps = max(1, args.steps)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(steps):
+        net.forward(x, rgb, stream=stream)
+    ev1.record(stream)
+    stream.synchronize()
+    if un.status(stream) != 0:
+        raise RuntimeError("inpainter kernel status")
+    ms = ev0.elapsed_time(ev1) / steps
+    flops = W.flops_per_tile() * T
+    tflops = flops / (ms * 1e-3) / 1e12
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    peak = float(peaks.get("bf16_tflops", 1900.0))
+    # (2) the frame path on the quest pool
+    pool = make_pool(cfg, frame_seeds(0, 1, 4), "cuda")
+    hdl = yoro.yoro_create(**cfg.camera())
+    zt = torch.empty((cfg.h, cfg.w), dtype=torch.float32, device="cuda")
+    lat = []
+    for i in range(max(3, args.warmup) + 20):
+        f = pool[i % len(pool)]
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        yoro.yoro_synthesize_zt(hdl, f["color"], f["depth"], f["out"], f["mask"], zt, stream=stream)
+        net.inpaint(f["out"], f["mask"], zt, f["depth"], cfg.near, stream=stream)
+        b.record(stream)
+        stream.synchronize()
+        if i >= max(3, args.warmup):
+            lat.append(a.elapsed_time(b))
+    lat.sort()
+    yoro.yoro_destroy(hdl)
+    net.close()
+    print(json.dumps({
+        "metric": "learned inpainter: network TFLOP/s on 64x64 tiles; frame path ms (synthesis + inpainting)",
+        "value": round(tflops, 2), "unit": "TFLOP/s", "n_gpus": 1, "steps": steps, "warmup": args.warmup,
+        "ms_per_step": round(ms, 4), "higher_is_better": True, "dtype": "bf16 (fp32 accumulate)",
+        "data": "synthetic", "weights": weights_kind,
+        "config": {"workload": f"every 64x64 tile of a 1832x1920 frame ({T} tiles per step), 4-level U-Net "
+                               "32/64/128/256", "flops_per_tile": W.flops_per_tile(), "tiles": T},
+        "roofline": {"bound": "tensor", "achieved": round(tflops, 2), "peak": peak, "unit": "TFLOP/s",
+                     "frac": round(tflops / peak, 4), "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst)"},
+        "frame_path_ms": {"p50": round(lat[len(lat) // 2], 3), "p99": round(lat[int(0.99 * (len(lat) - 1))], 3),
+                          "what": "yoro_synthesize_zt + yoro_unet_inpaint on one 1832x1920 frame (hole tiles only)"},
+    }), flush=True)
+
+
 def _render_left(spec):
     from paper_2506_15183_gb300 import scene
 
@@ -556,6 +632,10 @@ def main():
     if args.workload in ("imbuffer", "pose"):
         if rank == 0:
             run_variant(args)
+        return
+    if args.workload == "inpaint":
+        if rank == 0:
+            run_inpaint(args)
         return
 
     import torch

@@ -150,3 +150,17 @@ def test_null_handle_and_strings(lib):
     lib.yoro_destroy(None)
     for code in range(7):
         assert lib.yoro_status_string(code)
+
+
+def test_inpainter_entry_points_check_arguments_without_a_gpu(lib):
+    """The inpainter's parameter count matches the package's layer table, and bad
+    arguments are refused before anything touches the device."""
+    from paper_2506_15183_gb300 import unet, weights
+
+    assert unet.param_count() == weights.count()
+    L = unet._lib_net()
+    assert not L.yoro_unet_create(None, weights.count(), 1, 64, 64)
+    # null pointers and unsupported shapes (Cout 48, Cin 16) of the layer call
+    assert L.yoro_unet_conv3x3(None, 1, 64, 64, 32, None, None, None, 32, 32, 0, 0, 1, None) == 1
+    assert L.yoro_unet_forward(None, None, 1, None, None) == 1
+    assert L.yoro_unet_inpaint(None, 64, 64, 0.05, None, None, None, None, None) == 1
