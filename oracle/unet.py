@@ -155,3 +155,111 @@ def compose(warped: np.ndarray, mask: np.ndarray, color: np.ndarray) -> np.ndarr
     out[..., :3][hole] = net[hole]
     out[..., 3][hole] = 255
     return out
+
+
+# ---- training: the loss and its gradient (test infrastructure for the GPU trainer) ----
+#
+# Loss of one batch: the mean over hole pixels and color channels of the squared error
+# between the network's color and the ground truth (in [0, 1]):
+#     L = sum_{hole pixels, c} (s_c - g_c)^2 / (3 * number of hole pixels).
+# The gradient is the chain rule through the network written out layer by layer (no
+# automatic differentiation): sigmoid' = s (1 - s); the 1x1 layer's transpose; ReLU'
+# = 1 where the layer's output is positive; a 3x3 convolution's data gradient is the
+# full correlation of the output gradient with the kernel flipped in both directions and
+# transposed in its channels, its weight gradient the correlation of the input with the
+# output gradient; 2x2 max pooling sends the gradient to the first maximum of its window
+# (row-major order); nearest upsampling sums the four gradients of a 2x2 block; a
+# concatenation splits the gradient by channels.  With exact=True every array is float64
+# and nothing is rounded to bfloat16 (the form the finite-difference pin checks); with
+# exact=False the forward is the definition's (bfloat16 activations), and the backward
+# runs in float64 through those activations.
+
+def _conv3x3_64(x, w, b):
+    c, h, wd = x.shape
+    xp = np.zeros((c, h + 2, wd + 2))
+    xp[:, 1:-1, 1:-1] = x
+    out = np.zeros((w.shape[0], h, wd))
+    for dy in range(3):
+        for dx in range(3):
+            out += np.einsum("kc,chw->khw", w[:, :, dy, dx], xp[:, dy:dy + h, dx:dx + wd])
+    return out + b[:, None, None]
+
+
+def _conv3x3_backward(x, w, dz):
+    """(dx, dw, db) of y = conv3x3(x, w) + b given dz = dL/dy (float64)."""
+    c, h, wd = x.shape
+    xp = np.zeros((c, h + 2, wd + 2))
+    xp[:, 1:-1, 1:-1] = x
+    dw = np.zeros(w.shape)
+    dxp = np.zeros((c, h + 2, wd + 2))
+    for dy in range(3):
+        for dx in range(3):
+            dw[:, :, dy, dx] = np.einsum("khw,chw->kc", dz, xp[:, dy:dy + h, dx:dx + wd])
+            dxp[:, dy:dy + h, dx:dx + wd] += np.einsum("kc,khw->chw", w[:, :, dy, dx], dz)
+    return dxp[:, 1:-1, 1:-1], dw, dz.sum(axis=(1, 2))
+
+
+def _maxpool_backward(x, dy):
+    """Gradient of 2x2 max pooling: each window's gradient to its first maximum (row-major)."""
+    c, h, w = x.shape
+    win = x.reshape(c, h // 2, 2, w // 2, 2).transpose(0, 1, 3, 2, 4).reshape(c, h // 2, w // 2, 4)
+    first = np.argmax(win == win.max(axis=-1, keepdims=True), axis=-1)
+    dx = np.zeros((c, h // 2, w // 2, 4))
+    np.put_along_axis(dx, first[..., None], dy[..., None], axis=-1)
+    return dx.reshape(c, h // 2, w // 2, 2, 2).transpose(0, 1, 3, 2, 4).reshape(c, h, w)
+
+
+def loss_and_grads(x: np.ndarray, p: dict, gt: np.ndarray, hole: np.ndarray, exact: bool = False):
+    """Loss (float) and gradients {name.w, name.b} (float64) of the network on tile x (6, H,
+    W), ground truth gt (3, H, W) in [0, 1] and hole mask (H, W)."""
+    f = (lambda a: np.asarray(a, np.float64)) if exact else (lambda a: bf16(a).astype(np.float64))
+    P = {k: (f(v) if k.endswith(".w") else np.asarray(v, np.float64)) for k, v in p.items()}
+    conv = _conv3x3_64 if exact else (lambda a, w, b: conv3x3(a.astype(np.float32), w.astype(np.float32),
+                                                             b.astype(np.float32)).astype(np.float64))
+    act = (lambda z: np.maximum(z, 0.0)) if exact else (lambda z: bf16(np.maximum(z, 0.0).astype(np.float32))
+                                                         .astype(np.float64))
+    a = f(x)
+    saved, skips = [], []
+    for l in range(len(WIDTHS)):
+        if l:
+            pooled_from = a
+            a = a.reshape(a.shape[0], a.shape[1] // 2, 2, a.shape[2] // 2, 2).max(axis=(2, 4))
+            saved.append(("pool", l, pooled_from))
+        for s in "ab":
+            y = act(conv(a, P[f"enc{l}{s}.w"], P[f"enc{l}{s}.b"]))
+            saved.append(("conv", f"enc{l}{s}", a, y))
+            a = y
+        skips.append(a)
+    for l in range(len(WIDTHS) - 2, -1, -1):
+        up = np.repeat(np.repeat(a, 2, axis=1), 2, axis=2)
+        saved.append(("cat", l, skips[l].shape[0]))
+        a = np.concatenate([skips[l], up], axis=0)
+        for s in "ab":
+            y = act(conv(a, P[f"dec{l}{s}.w"], P[f"dec{l}{s}.b"]))
+            saved.append(("conv", f"dec{l}{s}", a, y))
+            a = y
+    wo, bo = P["out.w"], P["out.b"]
+    z = np.einsum("kc,chw->khw", wo, a) + bo[:, None, None]
+    s_ = 1.0 / (1.0 + np.exp(-z))
+    m = hole.astype(bool)[None]
+    n = 3 * int(hole.astype(bool).sum())
+    err = np.where(m, s_ - gt, 0.0)
+    loss = float((err ** 2).sum() / n)
+    dzo = 2.0 * err / n * s_ * (1.0 - s_)
+    g = {"out.w": np.einsum("khw,chw->kc", dzo, a), "out.b": dzo.sum(axis=(1, 2))}
+    da = np.einsum("kc,khw->chw", wo, dzo)
+    skip_grads = {}
+    for item in reversed(saved):
+        if item[0] == "conv":
+            _, name, xin, y = item
+            dz = da * (y > 0)
+            da, g[name + ".w"], g[name + ".b"] = _conv3x3_backward(xin, P[name + ".w"], dz)
+        elif item[0] == "cat":
+            _, l, cs = item
+            skip_grads[l] = da[:cs]
+            d_up = da[cs:]
+            da = d_up.reshape(d_up.shape[0], d_up.shape[1] // 2, 2, d_up.shape[2] // 2, 2).sum(axis=(2, 4))
+        else:  # pool of level l - 1's output: its window's first maximum, plus the skip path
+            _, l, src = item
+            da = _maxpool_backward(src, da) + skip_grads.pop(l - 1)
+    return loss, g

@@ -31,6 +31,7 @@
 #include "yoro.h"
 #include "yoro_internal.h"
 #include "yoro_unet.h"
+#include "unet_internal.h"
 
 namespace yoro {
 
@@ -360,7 +361,7 @@ unsigned unet_status_take()
 // for shapes it does not take.
 cudaError_t unet_conv3x3(const void* x, int T, int H, int W, int Cin, const void* wk, const float* bias, void* y,
                          int Cout, int y_cstride, int y_coff, int upsample, int relu, cudaStream_t stream,
-                         const int* count = nullptr)
+                         const int* count)
 {
     if (T < 1 || H < 1 || W < 1 || Cin < kKc || Cin % kKc || (Cout != 32 && Cout != 64 && Cout != 128 && Cout != 256))
         return cudaErrorInvalidValue;
@@ -621,7 +622,7 @@ __global__ void output_kernel(const uint16_t* __restrict__ a, const float* __res
     }
 }
 
-void host_bf16(const float* src, size_t n, uint16_t* dst)
+void host_bf16_impl(const float* src, size_t n, uint16_t* dst)
 {
     for (size_t i = 0; i < n; ++i) {
         uint32_t u;
@@ -637,23 +638,14 @@ void host_bf16(const float* src, size_t n, uint16_t* dst)
 
 }  // namespace
 
-// Parameters of the network: 14 3x3 layers (enc0a, enc0b, ..., enc3b, dec2a, dec2b, dec1a,
-// dec1b, dec0a, dec0b) and the 1x1 output layer, in the order of the definition.
-struct UnetLayer {
-    int cin, cout, cin_pad;
-    uint16_t* wk;  // device, K-major bfloat16
-    float* bias;   // device
-};
+void host_bf16(const float* src, size_t n, uint16_t* dst) { host_bf16_impl(src, n, dst); }
 
-struct UnetNet {
-    UnetLayer conv[14];
-    float* wout;  // device: 3 x 32 (bfloat16 values as floats), then 3 biases
-    int max_tiles;
-    // activations, NHWC bfloat16, for max_tiles tiles
-    uint16_t *in0, *e0a, *cat0, *p0, *e1a, *cat1, *p1, *e2a, *cat2, *p2, *e3a, *d2a, *d1a, *d0a, *d0b;
-    int *flags, *list, *count;
-    int max_grid_tiles;  // capacity of flags / list
-};
+cudaError_t unet_output_rgb(const UnetNet* n, int T, float* rgb, cudaStream_t s)
+{
+    output_kernel<<<dim3(16, (unsigned)T), 256, 0, s>>>(n->d0b, n->wout, n->wout + 96, T, nullptr, 0, rgb, nullptr, 0,
+                                                      0, 0, nullptr, nullptr);
+    return cudaGetLastError();
+}
 
 size_t unet_param_count()
 {
@@ -670,7 +662,7 @@ size_t unet_param_count()
     return n + 3 * 32 + 3;
 }
 
-static void layer_dims(int i, int* cin, int* cout)
+void unet_layer_dims(int i, int* cin, int* cout)
 {
     // i = 0..7 encoder (level i / 2), 8..13 decoder (levels 2, 1, 0)
     if (i < 8) {
@@ -713,7 +705,7 @@ UnetNet* unet_create(const float* params, size_t n_params, int max_tiles, int ma
     std::vector<uint16_t> hk;
     for (int i = 0; i < 14 && ok; ++i) {
         int cin, cout;
-        layer_dims(i, &cin, &cout);
+        unet_layer_dims(i, &cin, &cout);
         UnetLayer& L = n->conv[i];
         L.cin = cin;
         L.cout = cout;
