@@ -91,6 +91,34 @@ yoro_status yoro_unet_inpaint(yoro_unet u, int w, int h, float near_, void* rgba
                               const float* zt, const float* src_depth, void* cuda_stream);
 
 /*
+ * Training on the GPU (all in this library's kernels: the forward above, the loss, the
+ * backward pass and Adam).  Loss of a batch: the mean over hole pixels and color channels
+ * of (s - g)^2, s the network's color and g = ground truth / 255.  The trainer keeps FP32
+ * master weights, Adam moments and device buffers for batch_tiles tiles (batch_tiles
+ * even).  NULL on a wrong argument or a failed allocation.
+ */
+typedef struct yoro_unet_trainer_ctx* yoro_unet_trainer;
+yoro_unet_trainer yoro_unet_trainer_create(const float* params, long long n_params, int batch_tiles, float lr,
+                                           float beta1, float beta2, float eps);
+void yoro_unet_trainer_destroy(yoro_unet_trainer t);
+
+/*
+ * One step on `tiles` tiles (even, <= batch_tiles): x as for yoro_unet_forward(); gt:
+ * tiles x 64 x 64 x 3 bytes (the ground-truth colors); hole: tiles x 64 x 64 bytes (1 =
+ * the pixel counts in the loss).  Device pointers.  With lr = 0 the weights do not move
+ * and the step's gradients can be read.
+ */
+yoro_status yoro_unet_train_step(yoro_unet_trainer t, const void* x, const unsigned char* gt,
+                                 const unsigned char* hole, int tiles, void* cuda_stream);
+
+/*
+ * Copy to host memory, after the work on cuda_stream: what = 0 the master weights, 1 the
+ * last step's gradients (yoro_unet_param_count() floats each, the parameter order), 2 the
+ * last step's loss (one float).  Synchronises the stream.
+ */
+yoro_status yoro_unet_trainer_read(yoro_unet_trainer t, int what, float* host_out, void* cuda_stream);
+
+/*
  * Synchronise cuda_stream and report the inpainter kernels' status: YORO_ECUDA if CUDA
  * reports an error, YORO_EDEVICE if a kernel gave up an internal wait (the record is
  * read and cleared), else YORO_OK.

@@ -28,7 +28,7 @@ BUILD = os.path.join(ROOT, "_build")
 LIBDIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(LIBDIR, "libyoro.so")
 DEBUG_LIB = os.path.join(LIBDIR, "libyoro_debug.so")
-SOURCES = ["api.cu", "fused.cu", "unfused.cu", "noalloc.cu", "server.cu", "imbuffer.cu", "pose.cu", "unet.cu"]
+SOURCES = ["api.cu", "fused.cu", "unfused.cu", "noalloc.cu", "server.cu", "imbuffer.cu", "pose.cu", "unet.cu", "unet_train.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-fmad=false", "-Xcompiler", "-fPIC",
               "-Xptxas", "-v", f"-I{INCLUDE}", f"-I{CSRC}"]

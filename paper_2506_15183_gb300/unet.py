@@ -145,3 +145,60 @@ class Inpainter:
             self.close()
         except Exception:  # noqa: BLE001 - interpreter shutdown
             pass
+
+
+def _lib_train():
+    lib = _lib_net()
+    if not hasattr(lib, "_train_declared"):
+        P, I, F, L = ctypes.c_void_p, ctypes.c_int, ctypes.c_float, ctypes.c_longlong
+        lib.yoro_unet_trainer_create.argtypes = [P, L, I, F, F, F, F]
+        lib.yoro_unet_trainer_create.restype = P
+        lib.yoro_unet_trainer_destroy.argtypes = [P]
+        lib.yoro_unet_trainer_destroy.restype = None
+        lib.yoro_unet_train_step.argtypes = [P, P, P, P, I, P]
+        lib.yoro_unet_train_step.restype = I
+        lib.yoro_unet_trainer_read.argtypes = [P, I, P, P]
+        lib.yoro_unet_trainer_read.restype = I
+        lib._train_declared = True
+    return lib
+
+
+class Trainer:
+    """yoro_unet_trainer_*: Adam on the GPU from an initial parameter array."""
+
+    def __init__(self, params: np.ndarray, batch_tiles: int, lr: float = 1e-3, beta1: float = 0.9,
+                 beta2: float = 0.999, eps: float = 1e-8):
+        params = np.ascontiguousarray(params, np.float32)
+        self.n = params.size
+        self.ptr = _lib_train().yoro_unet_trainer_create(params.ctypes.data, params.size, int(batch_tiles), lr, beta1,
+                                                         beta2, eps)
+        if not self.ptr:
+            raise RuntimeError("yoro_unet_trainer_create failed")
+
+    def step(self, x: torch.Tensor, gt: torch.Tensor, hole: torch.Tensor, stream=None) -> None:
+        T = x.shape[0]
+        if tuple(x.shape) != (T, 64, 64, 32):
+            raise ValueError("x must be (T, 64, 64, 32) bf16")
+        for t, shp, name in ((gt, (T, 64, 64, 3), "gt"), (hole, (T, 64, 64), "hole")):
+            if not t.is_cuda or t.dtype != torch.uint8 or tuple(t.shape) != shp or not t.is_contiguous():
+                raise ValueError(f"{name} must be a contiguous CUDA uint8 tensor {shp}")
+        _check(_lib_train().yoro_unet_train_step(self.ptr, _bf16_ptr(x, "x"), gt.data_ptr(), hole.data_ptr(), T,
+                                                 _stream(stream)), "yoro_unet_train_step")
+
+    def read(self, what: str, stream=None) -> np.ndarray:
+        code = {"params": 0, "grads": 1, "loss": 2}[what]
+        out = np.empty(1 if code == 2 else self.n, np.float32)
+        _check(_lib_train().yoro_unet_trainer_read(self.ptr, code, out.ctypes.data, _stream(stream)),
+               "yoro_unet_trainer_read")
+        return out
+
+    def close(self) -> None:
+        if self.ptr:
+            _lib_train().yoro_unet_trainer_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001 - interpreter shutdown
+            pass
