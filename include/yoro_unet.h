@@ -91,6 +91,17 @@ yoro_status yoro_unet_inpaint(yoro_unet u, int w, int h, float near_, void* rgba
                               const float* zt, const float* src_depth, void* cuda_stream);
 
 /*
+ * The network inputs of a frame's hole tiles, as yoro_unet_inpaint() builds them: x_out
+ * receives the count tiles (count x 64 x 64 x 32 bfloat16, 16-byte aligned, room for
+ * max_out >= the frame's ceil(w/64) * ceil(h/64) tiles), list_host the tiles' indices
+ * ty * ceil(w/64) + tx in order and count_host their number.  Synchronises the stream
+ * (the host learns the count).  For building training sets.
+ */
+yoro_status yoro_unet_prepare(yoro_unet u, int w, int h, float near_, const void* rgba, const unsigned char* mask,
+                              const float* zt, const float* src_depth, void* x_out, int max_out, int* list_host,
+                              int* count_host, void* cuda_stream);
+
+/*
  * Training on the GPU (all in this library's kernels: the forward above, the loss, the
  * backward pass and Adam).  Loss of a batch: the mean over hole pixels and color channels
  * of (s - g)^2, s the network's color and g = ground truth / 255.  The trainer keeps FP32
@@ -117,6 +128,9 @@ yoro_status yoro_unet_train_step(yoro_unet_trainer t, const void* x, const unsig
  * last step's loss (one float).  Synchronises the stream.
  */
 yoro_status yoro_unet_trainer_read(yoro_unet_trainer t, int what, float* host_out, void* cuda_stream);
+
+/* The Adam step size of the following steps (>= 0). */
+yoro_status yoro_unet_trainer_set_lr(yoro_unet_trainer t, float lr);
 
 /*
  * Synchronise cuda_stream and report the inpainter kernels' status: YORO_ECUDA if CUDA

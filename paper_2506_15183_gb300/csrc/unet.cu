@@ -891,6 +891,35 @@ yoro_status yoro_unet_inpaint(yoro_unet u, int w, int h, float near_, void* rgba
     return cudaGetLastError() == cudaSuccess ? YORO_OK : YORO_ECUDA;
 }
 
+yoro_status yoro_unet_prepare(yoro_unet u, int w, int h, float near_, const void* rgba, const unsigned char* mask,
+                              const float* zt, const float* src_depth, void* x_out, int max_out, int* list_host,
+                              int* count_host, void* cuda_stream)
+{
+    if (!u || w < 0 || h < 0 || !(near_ > 0.0f) || !std::isfinite(near_) || !list_host || !count_host)
+        return YORO_EINVAL;
+    *count_host = 0;
+    if ((size_t)w * h == 0) return YORO_OK;
+    if (w > u->max_w || h > u->max_h) return YORO_ETOOBIG;
+    const int ntx = (w + 63) / 64, nty = (h + 63) / 64;
+    if (!rgba || !mask || !zt || !src_depth || !x_out || max_out < ntx * nty) return YORO_EINVAL;
+    if (((uintptr_t)rgba | (uintptr_t)zt | (uintptr_t)src_depth) & 3u || ((uintptr_t)x_out & 15u)) return YORO_EALIGN;
+    yoro::UnetNet* n = u->net;
+    const cudaStream_t s = (cudaStream_t)cuda_stream;
+    yoro::tile_flags_kernel<<<dim3(ntx, nty), 256, 0, s>>>(mask, w, h, ntx, n->flags);
+    yoro::tile_list_kernel<<<1, 1024, 0, s>>>(n->flags, ntx * nty, n->list, n->count);
+    yoro::tile_input_kernel<<<dim3(16, (unsigned)(ntx * nty)), 256, 0, s>>>(
+        static_cast<const uint32_t*>(rgba), mask, zt, src_depth, w, h, ntx, near_, n->list, n->count,
+        static_cast<uint16_t*>(x_out));
+    if (cudaGetLastError() != cudaSuccess) return YORO_ECUDA;
+    if (cudaMemcpyAsync(count_host, n->count, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(list_host, n->list, (size_t)ntx * nty * 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaGetLastError();
+        return YORO_ECUDA;
+    }
+    return YORO_OK;
+}
+
 yoro_status yoro_unet_status(void* cuda_stream)
 {
     if (cudaStreamSynchronize((cudaStream_t)cuda_stream) != cudaSuccess) {

@@ -570,6 +570,13 @@ yoro_status yoro_unet_train_step(yoro_unet_trainer tr, const void* x, const unsi
                                                                                                  : YORO_ECUDA;
 }
 
+yoro_status yoro_unet_trainer_set_lr(yoro_unet_trainer tr, float lr)
+{
+    if (!tr || !(lr >= 0.0f) || !std::isfinite(lr)) return YORO_EINVAL;
+    tr->t->lr = lr;
+    return YORO_OK;
+}
+
 yoro_status yoro_unet_trainer_read(yoro_unet_trainer tr, int what, float* host_out, void* cuda_stream)
 {
     if (!tr || !host_out || what < 0 || what > 2) return YORO_EINVAL;

@@ -14,6 +14,8 @@ Workloads (shapes, sizes and distributions of the method's VR setting):
   y = -1.6 m, front depth log-uniform in 0.1-100 m.
 * ``batch_configs``: 64 frames, 16 each of 1024x1024, 1440x1600, 1832x1920 and
   2064x2208, 50-300 primitives each, IPD uniform in 0.055-0.072 m.
+* ``crop_config``: a centred 512x512 crop of the 1832x1920 camera (fx = 916) with the
+  quest scene's statistics (the learned inpainter's training frames).
 
 All use a 90 degree horizontal field of view (fx = fy = W/2), the principal point at
 the image centre, near 0.05 m and far 1000 m; the source is the left eye at the
@@ -83,10 +85,11 @@ class SceneConfig:
     far: float = 1000.0
     ground_y: float = -1.6
     max_cover: float = 0.25
+    focal: float = 0.0  # 0: W/2 (90 degree horizontal FOV); else fx = fy = focal (a centred crop of a wider camera)
 
     @property
     def fx(self) -> float:
-        return self.w / 2.0  # 90 degree horizontal FOV: (W/2) / tan(45 deg)
+        return self.focal if self.focal > 0 else self.w / 2.0  # 90 degree horizontal FOV: (W/2) / tan(45 deg)
 
     @property
     def fy(self) -> float:
@@ -118,6 +121,14 @@ def quest_config() -> SceneConfig:
 
 
 BATCH_SIZES = ((1024, 1024), (1440, 1600), (1832, 1920), (2064, 2208))
+
+
+def crop_config(side: int = 512) -> SceneConfig:
+    """The centred side x side crop of the 1832x1920 camera (fx = fy = 916, the same
+    disparities and hole widths), with the quest scene's statistics: the inpainter's
+    training frames."""
+    q = quest_config()
+    return q.replace(w=side, h=side, focal=q.fx)
 
 
 def batch_configs(n_frames: int = 64, seed0: int = 1000):

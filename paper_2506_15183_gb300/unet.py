@@ -86,6 +86,8 @@ def _lib_net():
         lib.yoro_unet_forward.restype = I
         lib.yoro_unet_inpaint.argtypes = [P, I, I, F, P, P, P, P, P]
         lib.yoro_unet_inpaint.restype = I
+        lib.yoro_unet_prepare.argtypes = [P, I, I, F, P, P, P, P, P, I, P, P, P]
+        lib.yoro_unet_prepare.restype = I
         lib._net_declared = True
     return lib
 
@@ -135,6 +137,20 @@ class Inpainter:
                                             zt.data_ptr(), src_depth.data_ptr(), _stream(stream)),
                "yoro_unet_inpaint")
 
+    def prepare(self, rgba, mask, zt, src_depth, near: float, x_out: torch.Tensor, stream=None) -> np.ndarray:
+        """The network inputs of the frame's hole tiles into x_out[:count]; returns the tile
+        indices (ty * ceil(w / 64) + tx)."""
+        h, w = mask.shape
+        ntiles = ((w + 63) // 64) * ((h + 63) // 64)
+        if x_out.shape[0] < ntiles or tuple(x_out.shape[1:]) != (64, 64, 32):
+            raise ValueError("x_out must hold (>= tiles of the frame, 64, 64, 32)")
+        lst = np.zeros(ntiles, np.int32)
+        cnt = np.zeros(1, np.int32)
+        _check(_lib_net().yoro_unet_prepare(self.ptr, w, h, float(near), rgba.data_ptr(), mask.data_ptr(),
+                                            zt.data_ptr(), src_depth.data_ptr(), _bf16_ptr(x_out, "x_out"), ntiles,
+                                            lst.ctypes.data, cnt.ctypes.data, _stream(stream)), "yoro_unet_prepare")
+        return lst[:int(cnt[0])].copy()
+
     def close(self) -> None:
         if self.ptr:
             _lib_net().yoro_unet_destroy(self.ptr)
@@ -159,6 +175,8 @@ def _lib_train():
         lib.yoro_unet_train_step.restype = I
         lib.yoro_unet_trainer_read.argtypes = [P, I, P, P]
         lib.yoro_unet_trainer_read.restype = I
+        lib.yoro_unet_trainer_set_lr.argtypes = [P, F]
+        lib.yoro_unet_trainer_set_lr.restype = I
         lib._train_declared = True
     return lib
 
@@ -184,6 +202,9 @@ class Trainer:
                 raise ValueError(f"{name} must be a contiguous CUDA uint8 tensor {shp}")
         _check(_lib_train().yoro_unet_train_step(self.ptr, _bf16_ptr(x, "x"), gt.data_ptr(), hole.data_ptr(), T,
                                                  _stream(stream)), "yoro_unet_train_step")
+
+    def set_lr(self, lr: float) -> None:
+        _check(_lib_train().yoro_unet_trainer_set_lr(self.ptr, float(lr)), "yoro_unet_trainer_set_lr")
 
     def read(self, what: str, stream=None) -> np.ndarray:
         code = {"params": 0, "grads": 1, "loss": 2}[what]
