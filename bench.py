@@ -447,9 +447,12 @@ def run_serve(args):
     from paper_2506_15183_gb300 import scene
     from paper_2506_15183_gb300.server import Server
 
+    from paper_2506_15183_gb300 import unet as un
+    from paper_2506_15183_gb300 import weights as W
+
     sizes = [(1440, 1600), (1832, 1920), (2064, 2208)]
     rates = [72.0, 90.0, 120.0]
-    nstreams, poses, slots = 8, 8, 3
+    nstreams, poses, slots = 8, 32, 3
     rng = np.random.default_rng(2024)
     specs, streams = [], []
     for i in range(nstreams):
@@ -464,9 +467,12 @@ def run_serve(args):
         st["pool"] = [(torch.from_numpy(c).cuda(), torch.from_numpy(d).cuda()) for c, d in data[i * poses:(i + 1) * poses]]
     yoro.load_library()
     srv = Server(16 << 30, max_batch=64)
+    params, weights_kind = (W.load_flat(), "trained") if W.exists() else (W.init_params(1), "initial")
+    net = un.Inpainter(params, max_w=max(w for w, _ in sizes), max_h=max(h for _, h in sizes))
     copy_stream = torch.cuda.Stream()
-    for st in streams:
-        st["id"] = srv.admit(**st["cfg"].camera(), slots=slots)
+    for i, st in enumerate(streams):
+        st["learned"] = i % 2 == 1  # every other stream repaints its holes with the network
+        st["id"] = srv.admit(**st["cfg"].camera(), slots=slots, learned=st["learned"])
         st["views"] = [srv.slot(st["id"], k) for k in range(slots)]
 
     def run(seconds, paced):
@@ -475,6 +481,7 @@ def run_serve(args):
             st["next"] = 0.0
             st["lat"] = []
             st["n"] = 0
+            st["inpainted"] = 0
         t0 = time.perf_counter()
         submitted = completed = 0
         while True:
@@ -485,6 +492,7 @@ def run_serve(args):
                 st = streams[r.stream]
                 st["free"].append(r.slot)
                 st["lat"].append((r.done_ns - r.submit_ns) / 1e6)
+                st["inpainted"] += r.inpainted
                 completed += 1
             for st in streams:
                 if st["free"] and (not paced or now >= st["next"]):
@@ -506,27 +514,40 @@ def run_serve(args):
             streams[r.stream]["lat"].append((r.done_ns - r.submit_ns) / 1e6)
         return time.perf_counter() - t0
 
+    def report(secs):
+        out = []
+        for st in streams:
+            lat = sorted(st["lat"])
+            out.append({"w": st["cfg"].w, "h": st["cfg"].h, "hz": st["hz"], "learned": st["learned"],
+                        "frames": len(lat), "inpainted": st["inpainted"], "frames_per_s": round(len(lat) / secs, 1),
+                        "latency_ms_p50": round(lat[len(lat) // 2], 3) if lat else None,
+                        "latency_ms_p99": round(lat[int(0.99 * (len(lat) - 1))], 3) if lat else None})
+        return out
+
+    srv.set_inpainter(net)
     run(0.5, paced=True)  # warm-up
     secs = run(max(2.0, args.serve_seconds), paced=True)
-    per_stream = []
-    for st in streams:
-        lat = sorted(st["lat"])
-        per_stream.append({"w": st["cfg"].w, "h": st["cfg"].h, "hz": st["hz"], "frames": len(lat),
-                           "frames_per_s": round(len(lat) / secs, 1),
-                           "latency_ms_p50": round(lat[len(lat) // 2], 3) if lat else None,
-                           "latency_ms_p99": round(lat[int(0.99 * (len(lat) - 1))], 3) if lat else None})
+    per_stream = report(secs)
     sat_secs = run(2.0, paced=False)
     sat_frames = sum(len(st["lat"]) for st in streams)
     sat_px = sum(len(st["lat"]) * st["cfg"].w * st["cfg"].h for st in streams)
+    srv.drain(60000)
+    srv.set_inpainter(None)  # the fallback: learned streams keep the paper's fill
+    fb_secs = run(max(2.0, args.serve_seconds), paced=True)
+    fallback = report(fb_secs)
     srv.close()
+    net.close()
     print(json.dumps({
         "metric": "serving loop: 8 headset streams at their refresh rates (frames/s and submit-to-done latency)",
         "value": round(sum(p["frames_per_s"] for p in per_stream), 1), "unit": "frames/s", "n_gpus": 1,
         "higher_is_better": True, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "serve: 8 streams of 1440x1600, 1832x1920, 2064x2208 at 72/90/120 Hz; head x on a "
-                               "seeded random walk, 8 poses per stream rendered on the host; 3 resident slots per stream",
-                   "entry_point": "yoro_server_submit (continuous batching)", "paced_seconds": round(secs, 2)},
+                               "seeded random walk, 32 poses per stream rendered on the host; 3 resident slots per "
+                               "stream; streams 1, 3, 5, 7 with learned inpainting",
+                   "entry_point": "yoro_server_submit (continuous batching)", "paced_seconds": round(secs, 2),
+                   "inpainter_weights": weights_kind},
         "streams": per_stream,
+        "fallback_streams": fallback,
         "saturation": {"frames_per_s": round(sat_frames / sat_secs, 1), "mpix_per_s": round(sat_px / sat_secs / 1e6, 1),
                        "what": "every stream resubmits as soon as one of its 3 slots frees up (host loop, one thread)"},
     }), flush=True)

@@ -54,7 +54,9 @@ typedef enum {
     YORO_ENOMEM = 3,   /* a device or pinned-host allocation failed                       */
     YORO_ECUDA = 4,    /* a CUDA runtime call or kernel launch failed                     */
     YORO_EDEVICE = 5,  /* a kernel of the debug-bounds build skipped an out-of-range access */
-    YORO_ETOOBIG = 6   /* the frame exceeds a limit of the requested entry point          */
+    YORO_ETOOBIG = 6,  /* the frame exceeds a limit of the requested entry point          */
+    YORO_ETIMEOUT = 7, /* a wait with a time limit ran out (yoro_server_drain)           */
+    YORO_ECANCELED = 8 /* the request was cancelled before it ran (yoro_server_cancel)   */
 } yoro_status;
 
 /* One frame of a batch (yoro_synthesize_batch).  All pointers are device pointers. */

@@ -20,6 +20,7 @@
 #include <stddef.h>
 
 #include "yoro.h"
+#include "yoro_unet.h"
 
 #ifdef __cplusplus
 extern "C" {
@@ -35,8 +36,10 @@ typedef struct {
     long long submit_ns;         /* when yoro_server_submit queued it                       */
     long long launch_ns;         /* when the batch that held it was launched                */
     long long done_ns;           /* when the scheduler saw that batch complete              */
-    int batch_frames;            /* frames in that batch                                    */
-    yoro_status status;          /* YORO_OK, or the batch launch's error                    */
+    int batch_frames;            /* frames in that batch (0: cancelled before a launch)     */
+    yoro_status status;          /* YORO_OK, the batch launch's error, or YORO_ECANCELED    */
+    int inpainted;               /* 1: the learned inpainter repainted the holes; 0: the
+                                    paper's fill (plain streams, no inpainter, or fallback) */
 } yoro_completion;
 
 /*
@@ -62,6 +65,39 @@ void yoro_server_destroy(yoro_server s);
 int yoro_server_admit(yoro_server s, int w, int h, float fx, float fy, float cx, float cy, float ipd,
                       float near_, float far_, int slots);
 
+/*
+ * yoro_server_admit() with a choice of hole fill: learned = 1 gives each slot a warped-
+ * depth buffer too (4 more bytes per pixel against the budget), and the frames of the
+ * stream are repainted by the server's inpainter (yoro_server_set_inpainter) after the
+ * synthesis; learned = 0 is yoro_server_admit().  A learned frame keeps the paper's fill
+ * (its fallback) when no inpainter is set or the inpainter does not take its size; its
+ * completion says which (inpainted).
+ */
+int yoro_server_admit_ex(yoro_server s, int w, int h, float fx, float fy, float cx, float cy, float ipd,
+                         float near_, float far_, int slots, int learned);
+
+/*
+ * The learned inpainter (yoro_unet.h) that repaints the frames of learned streams, or
+ * NULL for none.  The server does not own it: keep it alive, and do not use it on other
+ * streams, until the server is destroyed or another one (or NULL) is set and the frames
+ * submitted before have completed (drain).  Takes effect from the next batch.
+ */
+yoro_status yoro_server_set_inpainter(yoro_server s, yoro_unet u);
+
+/*
+ * paused = 1: launch nothing new (frames already launched complete; frames submitted
+ * wait); paused = 0: resume.  A headset that is taken off, or a test of what waits.
+ */
+yoro_status yoro_server_pause(yoro_server s, int paused);
+
+/*
+ * Cancel the frames of `stream` that are queued and not launched: each completes at once
+ * with YORO_ECANCELED (batch_frames 0) and its slot is free again; frames already in a
+ * batch complete normally.  Returns how many were cancelled, or the negated status
+ * (-YORO_EINVAL for an unknown stream).
+ */
+int yoro_server_cancel(yoro_server s, int stream);
+
 /* Remove a stream: waits until its submitted frames are done, then frees its slots.
  * Its completions stay available to yoro_server_poll. */
 yoro_status yoro_server_leave(yoro_server s, int stream);
@@ -80,7 +116,7 @@ yoro_status yoro_server_submit(yoro_server s, int stream, int slot, unsigned lon
 int yoro_server_poll(yoro_server s, yoro_completion* out, int max);
 
 /* Block until every submitted frame is done (or the timeout in milliseconds passes);
- * YORO_OK, or YORO_ECUDA if the timeout passed first. */
+ * YORO_OK, or YORO_ETIMEOUT if the timeout passed first. */
 yoro_status yoro_server_drain(yoro_server s, int timeout_ms);
 
 /* Bytes of the budget in use by admitted streams. */

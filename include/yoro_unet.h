@@ -81,18 +81,21 @@ yoro_status yoro_unet_forward(yoro_unet u, const void* x, int T, float* rgb, voi
 /*
  * Learned inpainting of one synthesized frame, in place.  rgba (w x h RGBA8) holds the
  * right eye from yoro_synthesize_zt(); mask, zt: its hole mask and warped depth;
- * src_depth: the left eye's depth (the source).  Every 64 x 64 tile of the frame that
- * holds a hole pixel (edge tiles padded with zero inputs outside the frame) goes through
- * the network, and each hole pixel takes rint(clamp(c, 0, 1) * 255) per color and alpha
- * 255; reached pixels are not touched.  The tile list is built on the device (nothing
+ * src_depth: the left eye's depth (the source).  The frame is cut into 64 x 64 cells;
+ * every cell that holds a hole pixel goes through the network as a 64 x 64 window: the
+ * cell itself, or for the last column and row the window shifted inward to end at the
+ * frame's edge (so a window never leaves the frame; frames narrower or lower than 64 are
+ * padded with zero inputs).  Each hole pixel of the cell takes rint(clamp(c, 0, 1) * 255)
+ * per color and alpha 255; reached pixels are not touched.  The tile list is built on the device (nothing
  * is read back).  YORO_ETOOBIG if the frame exceeds the size the handle was created for.
  */
 yoro_status yoro_unet_inpaint(yoro_unet u, int w, int h, float near_, void* rgba, const unsigned char* mask,
                               const float* zt, const float* src_depth, void* cuda_stream);
 
 /*
- * The network inputs of a frame's hole tiles, as yoro_unet_inpaint() builds them: x_out
- * receives the count tiles (count x 64 x 64 x 32 bfloat16, 16-byte aligned, room for
+ * The network inputs of a frame's hole tiles, as yoro_unet_inpaint() builds them (the
+ * windows of the hole cells, shifted inward at the last column and row): x_out receives
+ * the count tiles (count x 64 x 64 x 32 bfloat16, 16-byte aligned, room for
  * max_out >= the frame's ceil(w/64) * ceil(h/64) tiles), list_host the tiles' indices
  * ty * ceil(w/64) + tx in order and count_host their number.  Synchronises the stream
  * (the host learns the count).  For building training sets.

@@ -29,7 +29,7 @@ _DEBUG_LIB_PATH = os.path.join(os.path.dirname(_LIB_PATH), "libyoro_debug.so")
 _lib = None
 
 STATUS = {0: "YORO_OK", 1: "YORO_EINVAL", 2: "YORO_EALIGN", 3: "YORO_ENOMEM", 4: "YORO_ECUDA",
-          5: "YORO_EDEVICE", 6: "YORO_ETOOBIG"}
+          5: "YORO_EDEVICE", 6: "YORO_ETOOBIG", 7: "YORO_ETIMEOUT", 8: "YORO_ECANCELED"}
 
 
 class YoroError(RuntimeError):

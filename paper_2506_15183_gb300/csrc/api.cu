@@ -452,7 +452,7 @@ yoro_status batch_validate(int n, const yoro_frame* frames, const FusedLimits& l
 // Launches validated frames, up to kMaxBatch per launch.  band_override > 0 sets the rows
 // per work item of every launch (it must fit the widest frame); 0 takes batch_band().
 yoro_status batch_launch(int n, const yoro_frame* frames, int dev, const FusedLimits& lim, int band_override,
-                         cudaStream_t stream)
+                         cudaStream_t stream, float* const* zt = nullptr)
 {
     yoro::BatchArgs* a = new (std::nothrow) yoro::BatchArgs;
     if (!a) return YORO_ENOMEM;
@@ -481,18 +481,35 @@ yoro_status batch_launch(int n, const yoro_frame* frames, int dev, const FusedLi
             int fb = band;
             while (fb < fr.h && yoro::fused_smem_bytes(yoro::fused_wpad(fr.w), fb + 1, 1) <= smem) ++fb;
             f.band = fb;
+            f.zt_out = zt ? zt[i] : nullptr;
             a->item_start[a->n] = a->total_items;
             a->f[a->n++] = f;
             a->total_items += (f.h + f.band - 1) / f.band;
         }
         a->item_start[a->n] = a->total_items;
-        if (a->n > 0 && yoro::fused_launch_batch(*a, wmax, lim, stream) != cudaSuccess) result = YORO_ECUDA;
+        if (a->n > 0 && yoro::fused_launch_batch(*a, wmax, lim, stream, zt != nullptr) != cudaSuccess)
+            result = YORO_ECUDA;
     }
     delete a;
     return result;
 }
 
 }  // namespace
+
+namespace yoro {
+int synthesize_batch_zt(int n, const yoro_frame* frames, float* const* zt, cudaStream_t stream)
+{
+    if (n < 0 || (n > 0 && !frames)) return YORO_EINVAL;
+    if (n > 4096) return YORO_ETOOBIG;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return YORO_ECUDA;
+    FusedLimits lim;
+    if (yoro::fused_configure(dev, &lim) != cudaSuccess) return YORO_ECUDA;
+    const yoro_status st = batch_validate(n, frames, lim, nullptr);
+    if (st != YORO_OK) return st;
+    return batch_launch(n, frames, dev, lim, 0, stream, zt);
+}
+}  // namespace yoro
 
 extern "C" {
 
@@ -627,6 +644,8 @@ const char* yoro_status_string(yoro_status s)
         case YORO_ECUDA: return "CUDA error";
         case YORO_EDEVICE: return "kernel reported an error";
         case YORO_ETOOBIG: return "frame exceeds a limit of this entry point";
+        case YORO_ETIMEOUT: return "a wait ran out of time";
+        case YORO_ECANCELED: return "cancelled before it ran";
     }
     return "unknown status";
 }

@@ -431,7 +431,7 @@ __device__ __forceinline__ void resolve_batch(const FrameArgs& f, const float* d
                 if (band && xin[q] && YORO_BOUND(vo + q * DX < f.h * w, kBadResolve)) {
                     if (reached) f.out[vo + q * DX] = cs[q][u];
                     f.mask[vo + q * DX] = reached ? 0 : 1;
-                    if (ZT) f.zt_out[vo + q * DX] = reached ? __uint_as_float(zbits) : 0.0f;
+                    if (ZT && f.zt_out) f.zt_out[vo + q * DX] = reached ? __uint_as_float(zbits) : 0.0f;
                 }
             }
         }
@@ -690,7 +690,7 @@ __global__ void __launch_bounds__(NT, MINB) fused_single(FrameArgs f, int wpad)
     }
 }
 
-template <int NT, int MINB>
+template <int NT, int MINB, bool ZT = false>
 __global__ void __launch_bounds__(NT, MINB) fused_batch(const __grid_constant__ BatchArgs a, int wpad)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -707,7 +707,7 @@ __global__ void __launch_bounds__(NT, MINB) fused_batch(const __grid_constant__ 
         // shared memory sized for max_band rows of the widest
         const Window s = window_layout(smem_raw, f.band + 2, (f.w + 7) / 8 * 8, f.w, ctr, rowinfo);
         const int y0 = (item - a.item_start[lo]) * f.band;
-        run_band<NT, false, false>(f, y0, min(y0 + f.band, f.h), s, ctr, rowinfo);
+        run_band<NT, false, ZT>(f, y0, min(y0 + f.band, f.h), s, ctr, rowinfo);
     }
 }
 
@@ -943,6 +943,7 @@ cudaError_t fused_configure(int device, FusedLimits* lim)
                          (const void*)fused_single<kBig, 1, true>,  (const void*)fused_single<kSmall, 2, true>,
                          (const void*)fused_single<kBig, 1, false, true>, (const void*)fused_single<kSmall, 2, false, true>,
                          (const void*)fused_batch<kBig, 1>,         (const void*)fused_batch<kSmall, 2>,
+                         (const void*)fused_batch<kBig, 1, true>,   (const void*)fused_batch<kSmall, 2, true>,
                          (const void*)fill_only<kBig>,              (const void*)imb_band<kBig>};
     for (const void* fn : fns) {
         e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
@@ -1003,7 +1004,7 @@ cudaError_t fused_launch(const FrameArgs& f, const FusedLimits& lim, int two_per
     return cudaGetLastError();
 }
 
-cudaError_t fused_launch_batch(const BatchArgs& a, int wmax, const FusedLimits& lim, cudaStream_t stream)
+cudaError_t fused_launch_batch(const BatchArgs& a, int wmax, const FusedLimits& lim, cudaStream_t stream, bool zt)
 {
     const int wpad = fused_wpad(wmax);
     const size_t smem = fused_smem_bytes(wpad, a.max_band, 1);  // batch frames use the default kernel
@@ -1013,10 +1014,13 @@ cudaError_t fused_launch_batch(const BatchArgs& a, int wmax, const FusedLimits& 
     // rest of the batch.
     const int grid = a.total_items;
     if (grid < 1) return cudaSuccess;
-    if (two)
-        fused_batch<kSmall, 2><<<grid, kSmall, smem, stream>>>(a, wpad);
-    else
-        fused_batch<kBig, 1><<<grid, kBig, smem, stream>>>(a, wpad);
+    if (two) {
+        if (zt) fused_batch<kSmall, 2, true><<<grid, kSmall, smem, stream>>>(a, wpad);
+        else fused_batch<kSmall, 2><<<grid, kSmall, smem, stream>>>(a, wpad);
+    } else {
+        if (zt) fused_batch<kBig, 1, true><<<grid, kBig, smem, stream>>>(a, wpad);
+        else fused_batch<kBig, 1><<<grid, kBig, smem, stream>>>(a, wpad);
+    }
     return cudaGetLastError();
 }
 

@@ -2,9 +2,12 @@
 // scheduler thread.  Contract in include/yoro_server.h.
 //
 // The scheduler keeps up to two batches in flight on its own CUDA stream: it launches
-// whatever is pending as one yoro_synthesize_batch, and while that runs, gathers the
-// frames submitted meanwhile into the next launch; it then waits (a blocking-sync CUDA
-// event, so the thread sleeps) for the older batch and reports its frames complete.
+// whatever is pending as one batched synthesis, and while that runs, gathers the frames
+// submitted meanwhile into the next launch; it then waits (a blocking-sync CUDA event, so
+// the thread sleeps) for the older batch and reports its frames complete.  Frames of
+// streams admitted with learned inpainting also get their warped depth from the batch,
+// and then, on the same CUDA stream, the server's inpainter repaints their holes; without
+// an inpainter (or for a frame larger than it takes) they keep the paper's fill.
 #include <cuda_runtime.h>
 
 #include <chrono>
@@ -19,6 +22,13 @@
 #include "yoro.h"
 #include "yoro_internal.h"
 #include "yoro_server.h"
+#include "yoro_unet.h"
+
+namespace yoro {
+// api.cu: yoro_synthesize_batch, where frame i with zt[i] set also writes its warped depth
+// there; returns a yoro_status.
+int synthesize_batch_zt(int n, const yoro_frame* frames, float* const* zt, cudaStream_t stream);
+}  // namespace yoro
 
 namespace {
 
@@ -35,6 +45,7 @@ struct Slot {
     float* depth;
     void* out;
     unsigned char* mask;
+    float* zt;  // warped depth (streams with learned inpainting), else null
     bool in_flight;
 };
 
@@ -46,12 +57,14 @@ struct Stream {
     unsigned char* block = nullptr;
     std::vector<Slot> slots;
     int pending = 0;  // submitted, not completed
+    bool learned = false;
 };
 
 struct Request {
     int stream, slot;
     unsigned long long tag;
     long long submit_ns;
+    int inpainted;
 };
 
 struct Batch {
@@ -78,6 +91,8 @@ struct yoro_server_ctx {
     std::vector<Stream> streams;
     long long outstanding = 0;  // submitted and not completed
     bool stop = false;
+    bool paused = false;
+    yoro_unet inpainter = nullptr;
     Batch ring[kInFlight];
     std::thread worker;
 
@@ -99,6 +114,7 @@ void yoro_server_ctx::complete(Batch& b, long long t_done)
             c.done_ns = t_done;
             c.batch_frames = (int)b.req.size();
             c.status = b.status;
+            c.inpainted = b.status == YORO_OK ? r.inpainted : 0;
             done.push_back(c);
             Stream& st = streams[r.stream];
             st.slots[r.slot].in_flight = false;
@@ -114,6 +130,8 @@ void yoro_server_ctx::run()
 {
     cudaSetDevice(device);
     std::vector<yoro_frame> frames;
+    std::vector<float*> zts;
+    yoro_unet net = nullptr;
     int head = 0, count = 0;  // ring of batches in flight: oldest at head
     for (;;) {
         // Launch a new batch when one can be in flight and work is pending; otherwise
@@ -123,10 +141,12 @@ void yoro_server_ctx::run()
             Batch& b = ring[(head + count) % kInFlight];
             {
                 std::unique_lock<std::mutex> lk(mu);
-                if (count == 0) cv_work.wait(lk, [&] { return stop || !pending.empty(); });
+                if (count == 0) cv_work.wait(lk, [&] { return stop || (!paused && !pending.empty()); });
                 if (pending.empty() && count == 0 && stop) break;
                 frames.clear();
-                while (!pending.empty() && (int)b.req.size() < max_batch) {
+                zts.clear();
+                net = inpainter;
+                while (!paused && !pending.empty() && (int)b.req.size() < max_batch) {
                     const Request r = pending.front();
                     pending.pop_front();
                     const Stream& st = streams[r.stream];
@@ -146,12 +166,25 @@ void yoro_server_ctx::run()
                     f.out_color = sl.out;
                     f.out_hole_mask = sl.mask;
                     frames.push_back(f);
+                    zts.push_back(st.learned ? sl.zt : nullptr);
                     b.req.push_back(r);
                 }
             }
             if (!b.req.empty()) {
                 b.launch_ns = now_ns();
-                b.status = yoro_synthesize_batch((int)frames.size(), frames.data(), cs);
+                bool any_learned = false;
+                for (float* z : zts) any_learned = any_learned || z != nullptr;
+                b.status = (yoro_status)yoro::synthesize_batch_zt((int)frames.size(), frames.data(),
+                                                                  any_learned ? zts.data() : nullptr, cs);
+                // learned inpainting of those frames, one after another on the same stream
+                for (size_t i = 0; i < b.req.size(); ++i) {
+                    b.req[i].inpainted = 0;
+                    if (b.status != YORO_OK || !zts[i] || !net) continue;
+                    const yoro_frame& f = frames[i];
+                    b.req[i].inpainted =
+                        yoro_unet_inpaint(net, f.w, f.h, f.near_, f.out_color, f.out_hole_mask, zts[i], f.depth, cs) ==
+                        YORO_OK;
+                }
                 if (b.status == YORO_OK && cudaEventRecord(b.done, cs) != cudaSuccess) b.status = YORO_ECUDA;
                 ++count;
                 launched = true;
@@ -230,6 +263,13 @@ void yoro_server_destroy(yoro_server s)
 int yoro_server_admit(yoro_server s, int w, int h, float fx, float fy, float cx, float cy, float ipd, float near_,
                       float far_, int slots)
 {
+    return yoro_server_admit_ex(s, w, h, fx, fy, cx, cy, ipd, near_, far_, slots, 0);
+}
+
+int yoro_server_admit_ex(yoro_server s, int w, int h, float fx, float fy, float cx, float cy, float ipd,
+                         float near_, float far_, int slots, int learned)
+{
+    if (learned != 0 && learned != 1) return -YORO_EINVAL;
     if (!s || slots < 1 || slots > kMaxSlots || !yoro::camera_valid(w, h, fx, fy, cx, cy, ipd, near_, far_) ||
         (size_t)w * (size_t)h == 0)
         return -YORO_EINVAL;
@@ -240,7 +280,7 @@ int yoro_server_admit(yoro_server s, int w, int h, float fx, float fy, float cx,
     }
     if (w > yoro_max_fused_width()) return -YORO_ETOOBIG;
     const size_t n = (size_t)w * (size_t)h;
-    const size_t per_slot = 3 * align256(4 * n) + align256(n);
+    const size_t per_slot = (learned ? 4 : 3) * align256(4 * n) + align256(n);
     const size_t bytes = per_slot * (size_t)slots;
     {
         std::lock_guard<std::mutex> lk(s->mu);
@@ -267,6 +307,7 @@ int yoro_server_admit(yoro_server s, int w, int h, float fx, float fy, float cx,
     st.far_ = far_;
     st.bytes = bytes;
     st.block = block;
+    st.learned = learned != 0;
     for (int i = 0; i < slots; ++i) {
         unsigned char* p = block + per_slot * (size_t)i;
         Slot sl;
@@ -274,6 +315,7 @@ int yoro_server_admit(yoro_server s, int w, int h, float fx, float fy, float cx,
         sl.depth = reinterpret_cast<float*>(p + align256(4 * n));
         sl.out = p + 2 * align256(4 * n);
         sl.mask = p + 3 * align256(4 * n);
+        sl.zt = learned ? reinterpret_cast<float*>(p + 3 * align256(4 * n) + align256(n)) : nullptr;
         sl.in_flight = false;
         st.slots.push_back(sl);
     }
@@ -328,7 +370,7 @@ yoro_status yoro_server_submit(yoro_server s, int stream, int slot, unsigned lon
         st.slots[slot].in_flight = true;
         ++st.pending;
         ++s->outstanding;
-        s->pending.push_back(Request{stream, slot, tag, now_ns()});
+        s->pending.push_back(Request{stream, slot, tag, now_ns(), 0});
     }
     s->cv_work.notify_one();
     return YORO_OK;
@@ -352,7 +394,62 @@ yoro_status yoro_server_drain(yoro_server s, int timeout_ms)
     std::unique_lock<std::mutex> lk(s->mu);
     const bool ok = s->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms < 0 ? 0 : timeout_ms),
                                         [&] { return s->outstanding == 0; });
-    return ok ? YORO_OK : YORO_ECUDA;
+    return ok ? YORO_OK : YORO_ETIMEOUT;
+}
+
+yoro_status yoro_server_set_inpainter(yoro_server s, yoro_unet u)
+{
+    if (!s) return YORO_EINVAL;
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->inpainter = u;
+    return YORO_OK;
+}
+
+yoro_status yoro_server_pause(yoro_server s, int paused)
+{
+    if (!s || (paused != 0 && paused != 1)) return YORO_EINVAL;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->paused = paused != 0;
+    }
+    s->cv_work.notify_all();
+    return YORO_OK;
+}
+
+int yoro_server_cancel(yoro_server s, int stream)
+{
+    if (!s) return -YORO_EINVAL;
+    int n = 0;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (stream < 0 || stream >= (int)s->streams.size() || !s->streams[stream].live) return -YORO_EINVAL;
+        Stream& st = s->streams[stream];
+        const long long t = now_ns();
+        for (auto it = s->pending.begin(); it != s->pending.end();) {
+            if (it->stream != stream) {
+                ++it;
+                continue;
+            }
+            yoro_completion c;
+            c.stream = it->stream;
+            c.slot = it->slot;
+            c.tag = it->tag;
+            c.submit_ns = it->submit_ns;
+            c.launch_ns = 0;
+            c.done_ns = t;
+            c.batch_frames = 0;
+            c.status = YORO_ECANCELED;
+            c.inpainted = 0;
+            s->done.push_back(c);
+            st.slots[it->slot].in_flight = false;
+            --st.pending;
+            --s->outstanding;
+            ++n;
+            it = s->pending.erase(it);
+        }
+    }
+    s->cv_done.notify_all();
+    return n;
 }
 
 size_t yoro_server_memory_used(yoro_server s)

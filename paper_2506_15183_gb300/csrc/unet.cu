@@ -491,10 +491,15 @@ __device__ __forceinline__ uint16_t bf16_bits(float v)
     return *reinterpret_cast<const uint16_t*>(&b);
 }
 
-// The network input of listed tile ti, pixel (py, px): the six channels of the
-// definition (warped color / 255 and 0 at holes, the hole mask, near / warped depth and
-// 0 at holes, near / source depth), rounded to bfloat16, then 26 zero channels.  Pixels
-// outside the frame (edge tiles) are all zero.
+// Origin of the 64 x 64 window of grid cell (tx, ty): the cell itself, except that the
+// last column and row are shifted inward so the window ends at the frame's edge (a frame
+// narrower or lower than 64 keeps origin 0 and is padded).  A tile writes its cell only.
+__device__ __forceinline__ int window_origin(int t, int size) { return max(0, min(kTile * t, size - kTile)); }
+
+// The network input of listed tile ti, pixel (py, px) of its window: the six channels of
+// the definition (warped color / 255 and 0 at holes, the hole mask, near / warped depth
+// and 0 at holes, near / source depth), rounded to bfloat16, then 26 zero channels.
+// Pixels outside the frame (frames smaller than a tile) are all zero.
 __global__ void tile_input_kernel(const uint32_t* __restrict__ rgba, const uint8_t* __restrict__ mask,
                                   const float* __restrict__ zt, const float* __restrict__ zsrc, int w, int h,
                                   int ntx, float near_, const int* __restrict__ list, const int* __restrict__ count,
@@ -505,7 +510,7 @@ __global__ void tile_input_kernel(const uint32_t* __restrict__ rgba, const uint8
     const int p = blockIdx.x * blockDim.x + threadIdx.x;  // pixel of the tile
     if (p >= kTile * kTile) return;
     const int tile = list[ti];
-    const int gx = (tile % ntx) * kTile + (p & (kTile - 1)), gy = (tile / ntx) * kTile + (p >> 6);
+    const int gx = window_origin(tile % ntx, w) + (p & (kTile - 1)), gy = window_origin(tile / ntx, h) + (p >> 6);
     float c[kInCh] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
     if (gx < w && gy < h) {
         const size_t o = (size_t)gy * w + gx;
@@ -570,7 +575,8 @@ __global__ void maxpool_kernel(const uint16_t* __restrict__ x, int T, int H, int
 // The output layer: a 1x1 convolution of the 32 channels (FP32 sums in channel order,
 // then the bias) and the logistic sigmoid 1 / (1 + exp(-z)).  mode 0: the three colors of
 // every pixel of every tile to rgb (T x 64 x 64 x 3 floats).  mode 1: compose into a frame:
-// each hole pixel of a listed tile takes rint(clamp(c, 0, 1) * 255) per color and alpha 255.
+// each hole pixel of a listed tile's cell takes rint(clamp(c, 0, 1) * 255) per color and
+// alpha 255 (the pixels of the window outside the cell belong to the neighbouring tile).
 __global__ void output_kernel(const uint16_t* __restrict__ a, const float* __restrict__ wo,
                               const float* __restrict__ bo, int T, const int* __restrict__ count, int mode,
                               float* __restrict__ rgb, const int* __restrict__ list, int ntx, int w, int h,
@@ -582,10 +588,10 @@ __global__ void output_kernel(const uint16_t* __restrict__ a, const float* __res
     if (p >= kTile * kTile) return;
     int gx = 0, gy = 0;
     if (mode == 1) {
-        const int tile = list[ti];
-        gx = (tile % ntx) * kTile + (p & (kTile - 1));
-        gy = (tile / ntx) * kTile + (p >> 6);
-        if (gx >= w || gy >= h || !mask[(size_t)gy * w + gx]) return;
+        const int tile = list[ti], tx = tile % ntx, ty = tile / ntx;
+        gx = window_origin(tx, w) + (p & (kTile - 1));
+        gy = window_origin(ty, h) + (p >> 6);
+        if (gx < kTile * tx || gy < kTile * ty || gx >= w || gy >= h || !mask[(size_t)gy * w + gx]) return;
     }
     const uint4* src = reinterpret_cast<const uint4*>(a + ((size_t)ti * kTile * kTile + p) * 32);
     float v[32];

@@ -75,7 +75,9 @@ cudaError_t fused_configure(int device, FusedLimits* lim);
 FusedShape fused_shape(const FusedLimits& lim, int w, int h, int halo = 1);
 int fused_max_band(const FusedLimits& lim, int w, int halo = 1);
 cudaError_t fused_launch(const FrameArgs& f, const FusedLimits& lim, int two_per_sm, cudaStream_t stream);
-cudaError_t fused_launch_batch(const BatchArgs& a, int wmax, const FusedLimits& lim, cudaStream_t stream);
+// zt: the instantiation that writes each frame's warped depth where its zt_out is set.
+cudaError_t fused_launch_batch(const BatchArgs& a, int wmax, const FusedLimits& lim, cudaStream_t stream,
+                               bool zt = false);
 
 // api.cu: the camera checks of yoro_create, and the status yoro_last_create_error reports.
 bool camera_valid(int w, int h, float fx, float fy, float cx, float cy, float ipd, float near_, float far_);

@@ -16,7 +16,7 @@ from . import YoroError, load_library
 class Completion(ctypes.Structure):
     _fields_ = [("stream", ctypes.c_int), ("slot", ctypes.c_int), ("tag", ctypes.c_ulonglong),
                 ("submit_ns", ctypes.c_longlong), ("launch_ns", ctypes.c_longlong), ("done_ns", ctypes.c_longlong),
-                ("batch_frames", ctypes.c_int), ("status", ctypes.c_int)]
+                ("batch_frames", ctypes.c_int), ("status", ctypes.c_int), ("inpainted", ctypes.c_int)]
 
 
 def _lib():
@@ -42,6 +42,14 @@ def _lib():
         lib.yoro_server_drain.restype = I
         lib.yoro_server_memory_used.argtypes = [P]
         lib.yoro_server_memory_used.restype = ctypes.c_size_t
+        lib.yoro_server_admit_ex.argtypes = [P, I, I, F, F, F, F, F, F, F, I, I]
+        lib.yoro_server_admit_ex.restype = I
+        lib.yoro_server_set_inpainter.argtypes = [P, P]
+        lib.yoro_server_set_inpainter.restype = I
+        lib.yoro_server_pause.argtypes = [P, I]
+        lib.yoro_server_pause.restype = I
+        lib.yoro_server_cancel.argtypes = [P, I]
+        lib.yoro_server_cancel.restype = I
         lib._server_typed = True
     return lib
 
@@ -62,9 +70,11 @@ class Server:
             raise YoroError(lib.yoro_last_create_error(), "yoro_server_create")
         self._shapes = {}
 
-    def admit(self, w, h, fx, fy, cx, cy, ipd, near=0.05, far=1000.0, slots=2) -> int:
-        """Stream id, or raises YoroError (YORO_ENOMEM when the budget is full)."""
-        r = _lib().yoro_server_admit(self._s, int(w), int(h), fx, fy, cx, cy, ipd, near, far, int(slots))
+    def admit(self, w, h, fx, fy, cx, cy, ipd, near=0.05, far=1000.0, slots=2, learned=False) -> int:
+        """Stream id, or raises YoroError (YORO_ENOMEM when the budget is full).  learned:
+        the stream's holes are repainted by the server's inpainter (set_inpainter)."""
+        r = _lib().yoro_server_admit_ex(self._s, int(w), int(h), fx, fy, cx, cy, ipd, near, far, int(slots),
+                                        int(bool(learned)))
         if r < 0:
             raise YoroError(-r, "yoro_server_admit")
         self._shapes[r] = (int(h), int(w))
@@ -104,6 +114,23 @@ class Server:
         st = _lib().yoro_server_drain(self._s, int(timeout_ms))
         if st != 0:
             raise YoroError(st, "yoro_server_drain")
+
+    def set_inpainter(self, inpainter) -> None:
+        """An Inpainter (paper_2506_15183_gb300.unet) or None; the caller keeps it alive."""
+        st = _lib().yoro_server_set_inpainter(self._s, inpainter.ptr if inpainter is not None else None)
+        if st != 0:
+            raise YoroError(st, "yoro_server_set_inpainter")
+
+    def pause(self, paused: bool = True) -> None:
+        st = _lib().yoro_server_pause(self._s, int(bool(paused)))
+        if st != 0:
+            raise YoroError(st, "yoro_server_pause")
+
+    def cancel(self, stream: int) -> int:
+        n = _lib().yoro_server_cancel(self._s, int(stream))
+        if n < 0:
+            raise YoroError(-n, "yoro_server_cancel")
+        return n
 
     def memory_used(self) -> int:
         return int(_lib().yoro_server_memory_used(self._s))

@@ -146,3 +146,141 @@ def test_leaving_with_frames_in_flight_completes_them_first(srv):
     assert [r.tag for r in s.poll()] == [50]
     assert np.array_equal(co.cpu().numpy(), ref[0]) and np.array_equal(mo.cpu().numpy(), ref[1])
     s.close()
+
+
+# ---- learned inpainting in the serving loop, and host-side faults --------------------
+
+def _fill_slot(s, sid, k, c, d):
+    ci, di, _, _ = s.slot(sid, k)
+    ci.copy_(torch.from_numpy(c))
+    di.copy_(torch.from_numpy(d))
+
+
+def _small(i):
+    cfg = scene.small_config().replace(w=256 + 64 * (i % 2), h=256, ipd=0.06 + 0.002 * i)
+    c, d, _ = scene.render(cfg, 700 + i)
+    return cfg, c, d
+
+
+def test_learned_stream_in_the_mix_equals_the_frame_alone(srv):
+    """A stream with learned inpainting shares batches with plain streams: its frame gets
+    the bytes of yoro_synthesize_zt + yoro_unet_inpaint on the frame alone, the plain
+    frames the oracle's, and each completion says which fill it got."""
+    import paper_2506_15183_gb300 as y
+    from paper_2506_15183_gb300 import unet as un
+    from paper_2506_15183_gb300 import weights as W
+
+    net = un.Inpainter(W.init_params(4), max_w=320, max_h=256)
+    frames = [_small(i) for i in range(3)]
+    # alone
+    cfg, c, d = frames[1]
+    hdl = y.yoro_create(**cfg.camera())
+    rgba = torch.empty((cfg.h, cfg.w, 4), dtype=torch.uint8, device="cuda")
+    mask = torch.empty((cfg.h, cfg.w), dtype=torch.uint8, device="cuda")
+    zt = torch.empty((cfg.h, cfg.w), dtype=torch.float32, device="cuda")
+    dg = torch.from_numpy(d).cuda()
+    y.yoro_synthesize_zt(hdl, torch.from_numpy(c).cuda(), dg, rgba, mask, zt)
+    net.inpaint(rgba, mask, zt, dg, cfg.near)
+    torch.cuda.synchronize()
+    alone = rgba.cpu().numpy()
+    y.yoro_destroy(hdl)
+    # in the mix
+    s = srv.Server(1 << 30, max_batch=8)
+    s.set_inpainter(net)
+    ids = [s.admit(**f[0].camera(), slots=2, learned=(i == 1)) for i, f in enumerate(frames)]
+    for sid, (fcfg, fc, fd) in zip(ids, frames):
+        _fill_slot(s, sid, 0, fc, fd)
+    torch.cuda.synchronize()
+    for k, sid in enumerate(ids):
+        s.submit(sid, 0, tag=k)
+    s.drain()
+    done = {r.tag: r for r in s.poll()}
+    assert all(done[k].status == 0 for k in range(3))
+    assert [done[k].inpainted for k in range(3)] == [0, 1, 0]
+    assert np.array_equal(s.slot(ids[1], 0)[2].cpu().numpy(), alone)
+    assert not np.array_equal(alone, oracle.synthesize(c, d, cfg.fx, cfg.fy, cfg.cx, cfg.cy, cfg.ipd, cfg.near,
+                                                       cfg.far)[0])  # the network did repaint
+    for i in (0, 2):
+        fcfg, fc, fd = frames[i]
+        ref = oracle.synthesize(fc, fd, fcfg.fx, fcfg.fy, fcfg.cx, fcfg.cy, fcfg.ipd, fcfg.near, fcfg.far)
+        assert np.array_equal(s.slot(ids[i], 0)[2].cpu().numpy(), ref[0])
+    s.close()
+    net.close()
+
+
+def test_learned_stream_without_an_inpainter_keeps_the_papers_fill(srv):
+    cfg, c, d = _small(0)
+    s = srv.Server(1 << 30, max_batch=4)
+    a = s.admit(**cfg.camera(), slots=1, learned=True)
+    _fill_slot(s, a, 0, c, d)
+    torch.cuda.synchronize()
+    s.submit(a, 0, tag=1)
+    s.drain()
+    (r,) = s.poll()
+    assert r.status == 0 and r.inpainted == 0
+    ref = oracle.synthesize(c, d, cfg.fx, cfg.fy, cfg.cx, cfg.cy, cfg.ipd, cfg.near, cfg.far)
+    assert np.array_equal(s.slot(a, 0)[2].cpu().numpy(), ref[0])
+    s.close()
+
+
+def test_drain_times_out_while_nothing_can_run(srv):
+    """The scheduler is paused, so a submitted frame cannot complete: drain() gives up
+    after its time limit with YORO_ETIMEOUT; resumed, the frame completes normally."""
+    import paper_2506_15183_gb300 as y
+
+    cfg, c, d = _small(1)
+    s = srv.Server(1 << 30, max_batch=4)
+    a = s.admit(**cfg.camera(), slots=1)
+    _fill_slot(s, a, 0, c, d)
+    torch.cuda.synchronize()
+    s.pause(True)
+    s.submit(a, 0, tag=9)
+    with pytest.raises(y.YoroError) as e:
+        s.drain(50)
+    assert e.value.code == 7  # YORO_ETIMEOUT
+    assert s.poll() == []
+    s.pause(False)
+    s.drain()
+    (r,) = s.poll()
+    assert r.tag == 9 and r.status == 0
+    s.close()
+
+
+def test_cancel_drops_queued_frames_and_frees_their_slots(srv):
+    import paper_2506_15183_gb300 as y
+
+    cfg, c, d = _small(2)
+    s = srv.Server(1 << 30, max_batch=4)
+    a = s.admit(**cfg.camera(), slots=3)
+    b = s.admit(**cfg.camera(), slots=1)
+    for k in range(3):
+        _fill_slot(s, a, k, c, d)
+    _fill_slot(s, b, 0, c, d)
+    torch.cuda.synchronize()
+    s.pause(True)
+    for k in range(3):
+        s.submit(a, k, tag=k)
+    s.submit(b, 0, tag=10)
+    assert s.cancel(a) == 3
+    done = s.poll()
+    assert sorted(r.tag for r in done) == [0, 1, 2]
+    assert all(r.status == 8 and r.batch_frames == 0 for r in done)  # YORO_ECANCELED
+    s.submit(a, 1, tag=11)  # the slot is free again
+    s.pause(False)
+    s.drain()
+    assert sorted(r.tag for r in s.poll()) == [10, 11]
+    with pytest.raises(y.YoroError):
+        s.cancel(99)
+    s.close()
+
+
+def test_an_oversized_frame_is_refused_at_admission(srv):
+    import paper_2506_15183_gb300 as y
+
+    s = srv.Server(1 << 34, max_batch=4)
+    w = y.yoro_max_fused_width() + 32
+    with pytest.raises(y.YoroError) as e:
+        s.admit(w=w, h=64, fx=w / 2, fy=w / 2, cx=w / 2, cy=32, ipd=0.063, slots=1)
+    assert e.value.code == 6  # YORO_ETOOBIG
+    assert s.memory_used() == 0
+    s.close()

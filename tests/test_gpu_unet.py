@@ -227,8 +227,9 @@ def test_every_layer_on_the_definitions_activations(un):
 
 @pytest.mark.parametrize("w,h", [(256, 256), (200, 136)])
 def test_inpaint_frame(un, w, h):
-    """The frame path: hole tiles found on the device, edge tiles padded with zero
-    inputs, hole pixels composed from the network's colors, everything else untouched.
+    """The frame path: hole cells found on the device, the last column's and row's windows
+    shifted inward to the frame's edge, hole pixels of each cell composed from the
+    network's colors, everything else untouched.
     Against the definition's compose() on the same tiles: reached pixels and hole-free
     tiles byte for byte; hole pixels within 8 levels, mean within 1 level."""
     import paper_2506_15183_gb300 as yoro
@@ -251,21 +252,20 @@ def test_inpaint_frame(un, w, h):
     net.inpaint(rgba, mask, zt, dg, cfg.near)
     assert un.status() == 0
     got = rgba.cpu().numpy()
-    # the definition on the zero-padded frame
-    W2, H2 = (w + 63) // 64 * 64, (h + 63) // 64 * 64
-    warped, m, z, ds = (_pad_to_tiles(a, h, w) for a in (st["warped"], st["mask"], st["zt"], d))
-    inside = _pad_to_tiles(np.ones((h, w), bool), h, w)
-    expect = _pad_to_tiles(plain, h, w)
-    for ty in range(H2 // 64):
-        for tx in range(W2 // 64):
-            sl = np.s_[64 * ty:64 * ty + 64, 64 * tx:64 * tx + 64]
-            if not m[sl].any():
+    # the definition on each hole cell's window: the cell, or for the last column and row
+    # the 64 x 64 window ending at the frame's edge; only the cell's pixels are written
+    expect = plain.copy()
+    for ty in range((h + 63) // 64):
+        for tx in range((w + 63) // 64):
+            cell = np.s_[64 * ty:64 * ty + 64, 64 * tx:64 * tx + 64]
+            if not st["mask"][cell].any():
                 continue
-            # an edge tile's pixels outside the frame are all-zero inputs (yoro_unet_inpaint)
-            xin = ref.tile_input(warped[sl], m[sl], z[sl], ds[sl], cfg.near) * inside[sl][None]
-            col = ref.forward(xin, p)
-            expect[sl] = ref.compose(expect[sl], m[sl], col)
-    expect = expect[:h, :w]
+            y0, x0 = min(64 * ty, h - 64), min(64 * tx, w - 64)
+            win = np.s_[y0:y0 + 64, x0:x0 + 64]
+            col = ref.forward(ref.tile_input(st["warped"][win], st["mask"][win], st["zt"][win], d[win], cfg.near), p)
+            comp = ref.compose(plain[win], st["mask"][win], col)
+            expect[cell] = comp[64 * ty - y0:64 * ty - y0 + 64, 64 * tx - x0:64 * tx - x0 + 64][
+                :expect[cell].shape[0], :expect[cell].shape[1]]
     hole = st["mask"].astype(bool)
     assert np.array_equal(got[~hole], plain[~hole])
     diff = np.abs(got[hole].astype(int) - expect[hole].astype(int))

@@ -90,7 +90,8 @@ UNET_MUTANTS = {
     "unet_bf16_truncates": ("r = ((u + 0x7FFF + lsb) >> 16) << 16", "r = (u >> 16) << 16"),
     "unet_bf16_ties_up": ("r = ((u + 0x7FFF + lsb) >> 16) << 16", "r = ((u + 0x8000) >> 16) << 16"),
     "unet_no_bias": ("    return acc + b[:, None, None]\n\n\ndef conv1x1", "    return acc\n\n\ndef conv1x1"),
-    "unet_padding_shifted": ("xp[:, 1:-1, 1:-1] = x", "xp[:, :-2, 1:-1] = x"),
+    "unet_padding_shifted": ("xp = np.zeros((c, h + 2, wd + 2), np.float32)\n    xp[:, 1:-1, 1:-1] = x",
+                             "xp = np.zeros((c, h + 2, wd + 2), np.float32)\n    xp[:, :-2, 1:-1] = x"),
     "unet_activations_not_rounded": ("return bf16(np.maximum(x, np.float32(0.0)))",
                                      "return np.maximum(x, np.float32(0.0))"),
 }
@@ -113,3 +114,35 @@ def test_inpainter_pins_catch_mutant(name, tmp_path):
                         os.path.join(ROOT, "tests", "test_oracle_unet.py")],
                        cwd=str(tmp_path), env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"mutant {name} passed every pin:\n{r.stdout[-2000:]}"
+
+
+# Mistakes planted in the definition of the inpainter's training gradient
+# (oracle/unet.py loss_and_grads); its finite-difference pin must catch each one.
+GRAD_MUTANTS = {
+    "grad_no_sigmoid_derivative": ("dzo = 2.0 * err / n * s_ * (1.0 - s_)", "dzo = 2.0 * err / n"),
+    "grad_kernel_not_flipped": ('dxp[:, dy:dy + h, dx:dx + wd] += np.einsum("kc,khw->chw", w[:, :, dy, dx], dz)',
+                                'dxp[:, dy:dy + h, dx:dx + wd] += np.einsum("kc,khw->chw", w[:, :, 2 - dy, 2 - dx], dz)'),
+    "grad_skip_path_dropped": ("da = _maxpool_backward(src, da) + skip_grads.pop(l - 1)",
+                               "da = _maxpool_backward(src, da) + 0 * skip_grads.pop(l - 1)"),
+    "grad_pool_to_window_corner": ("first = np.argmax(win == win.max(axis=-1, keepdims=True), axis=-1)",
+                                   "first = np.zeros(win.shape[:-1], int)"),
+    "grad_upsample_averaged": ("da = d_up.reshape(d_up.shape[0], d_up.shape[1] // 2, 2, d_up.shape[2] // 2, 2).sum(axis=(2, 4))",
+                               "da = d_up.reshape(d_up.shape[0], d_up.shape[1] // 2, 2, d_up.shape[2] // 2, 2).mean(axis=(2, 4))"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(GRAD_MUTANTS))
+def test_gradient_pin_catches_mutant(name, tmp_path):
+    import shutil
+
+    old, new = GRAD_MUTANTS[name]
+    src = open(UNET).read()
+    assert src.count(old) == 1, f"mutation site for {name} not found exactly once"
+    shutil.copytree(os.path.join(ROOT, "oracle"), tmp_path / "oracle",
+                    ignore=shutil.ignore_patterns("*.so", "__pycache__"))
+    (tmp_path / "oracle" / "unet.py").write_text(src.replace(old, new))
+    env = dict(os.environ, PYTHONPATH=f"{tmp_path}{os.pathsep}{ROOT}")
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        os.path.join(ROOT, "tests", "test_oracle_unet_grad.py") + "::test_gradient_matches_finite_differences"],
+                       cwd=str(tmp_path), env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode != 0, f"mutant {name} passed the gradient pin:\n{r.stdout[-2000:]}"
