@@ -7,7 +7,8 @@
  * 64 x 64 tiles that replaces the Patcher's colors at hole pixels, with the Patcher as
  * its fallback and its yardstick.  Its definition, written out on the CPU, is
  * oracle/unet.py:
- *   input    6 channels per pixel: warped color / 255 (zero at holes), the hole mask,
+ *   input    6 channels per pixel: the plain path's right eye / 255 (the warped colors,
+ *            and at holes the Patcher's fill, which the network refines), the hole mask,
  *            near / warped depth (zero at holes), near / source-eye depth;
  *   encoder  levels of 32, 64, 128, 256 channels, two 3x3 convolutions (zero padding)
  *            with ReLU each, 2x2 max pooling between levels;

@@ -7,9 +7,10 @@ The paper's Patcher is the hand-written fill of Alg. 3 and Eq. 6; a learned inpa
 is an extension of the method (its comparison system is a GAN, not reproduced).  The
 network defined here is a 4-level U-Net:
 
-  input    6 channels per pixel of a tile: the warped color (3, in [0, 1], zero at
-           holes), the hole mask (1 at holes), the warped depth and the source-eye depth
-           at the same pixel (each as near / depth, in (0, 1], zero where unknown)
+  input    6 channels per pixel of a tile: the plain path's right eye (3, in [0, 1]:
+           the warped color, and at holes the Patcher's fill, which the network refines),
+           the hole mask (1 at holes), the warped depth and the source-eye depth at the
+           same pixel (each as near / depth, in (0, 1]; the warped depth zero at holes)
   encoder  level l (l = 0..3, widths 32, 64, 128, 256): two 3x3 convolutions with zero
            padding, each followed by ReLU; between levels a 2x2 max pool
   decoder  level l (l = 2..0): nearest 2x upsampling of level l + 1, concatenated after
@@ -133,13 +134,15 @@ def forward(x: np.ndarray, p: dict) -> np.ndarray:
     return (np.float32(1.0) / (np.float32(1.0) + np.exp(-z, dtype=np.float32))).astype(np.float32)
 
 
-def tile_input(warped: np.ndarray, mask: np.ndarray, zt: np.ndarray, zsrc: np.ndarray, near: float) -> np.ndarray:
-    """The 6 input channels of a tile from the plain path's warped color (H, W, 4 uint8),
-    hole mask (H, W), warped depth zt (H, W; ignored at holes) and the source eye's
-    depth (H, W): color / 255 and near / depth (zero at holes for the warped depth)."""
+def tile_input(color: np.ndarray, mask: np.ndarray, zt: np.ndarray, zsrc: np.ndarray, near: float) -> np.ndarray:
+    """The 6 input channels of a tile from the plain path's right eye (H, W, 4 uint8: the
+    reached pixels' warped colors and the Patcher's fill at the holes), its hole mask
+    (H, W), warped depth zt (H, W; ignored at holes) and the source eye's depth (H, W):
+    color / 255 everywhere, the mask, and near / depth (zero at holes for the warped
+    depth)."""
     hole = mask.astype(bool)
     x = np.zeros((IN_CH,) + mask.shape, np.float32)
-    x[0:3] = np.where(hole[None], 0.0, warped[..., :3].transpose(2, 0, 1).astype(np.float32) / np.float32(255.0))
+    x[0:3] = color[..., :3].transpose(2, 0, 1).astype(np.float32) / np.float32(255.0)
     x[3] = hole.astype(np.float32)
     x[4] = np.where(hole, 0.0, np.float32(near) / np.maximum(zt, np.float32(near)))
     x[5] = np.float32(near) / np.maximum(zsrc, np.float32(near))

@@ -165,7 +165,7 @@ def test_forward_matches_definition(un):
     hole_tiles = [(ty, tx) for ty in range(4) for tx in range(4)
                   if st["mask"][64 * ty:64 * ty + 64, 64 * tx:64 * tx + 64].any()][:3]
     assert len(hole_tiles) == 3
-    xs = np.stack([ref.tile_input(st["warped"][64 * ty:64 * ty + 64, 64 * tx:64 * tx + 64],
+    xs = np.stack([ref.tile_input(st["out"][64 * ty:64 * ty + 64, 64 * tx:64 * tx + 64],
                                   st["mask"][64 * ty:64 * ty + 64, 64 * tx:64 * tx + 64],
                                   st["zt"][64 * ty:64 * ty + 64, 64 * tx:64 * tx + 64],
                                   d[64 * ty:64 * ty + 64, 64 * tx:64 * tx + 64], cfg.near)
@@ -192,7 +192,7 @@ def test_every_layer_on_the_definitions_activations(un):
     ty, tx = next((ty, tx) for ty in range(4) for tx in range(4)
                   if st["mask"][64 * ty:64 * ty + 64, 64 * tx:64 * tx + 64].any())
     sl = np.s_[64 * ty:64 * ty + 64, 64 * tx:64 * tx + 64]
-    x = ref.bf16(ref.tile_input(st["warped"][sl], st["mask"][sl], st["zt"][sl], d[sl], cfg.near))
+    x = ref.bf16(ref.tile_input(st["out"][sl], st["mask"][sl], st["zt"][sl], d[sl], cfg.near))
     p = {k: (ref.bf16(v) if k.endswith(".w") else v) for k, v in _weights(12).items()}
     layers = []  # (name, input (C, H, W), output (C, H, W))
     a, skips = x, []
@@ -262,7 +262,7 @@ def test_inpaint_frame(un, w, h):
                 continue
             y0, x0 = min(64 * ty, h - 64), min(64 * tx, w - 64)
             win = np.s_[y0:y0 + 64, x0:x0 + 64]
-            col = ref.forward(ref.tile_input(st["warped"][win], st["mask"][win], st["zt"][win], d[win], cfg.near), p)
+            col = ref.forward(ref.tile_input(st["out"][win], st["mask"][win], st["zt"][win], d[win], cfg.near), p)
             comp = ref.compose(plain[win], st["mask"][win], col)
             expect[cell] = comp[64 * ty - y0:64 * ty - y0 + 64, 64 * tx - x0:64 * tx - x0 + 64][
                 :expect[cell].shape[0], :expect[cell].shape[1]]

@@ -43,7 +43,7 @@ def _batch(seeds=(21, 22)):
         ty, tx = max(((ty, tx) for ty in range(4) for tx in range(4)),
                      key=lambda t: st["mask"][64 * t[0]:64 * t[0] + 64, 64 * t[1]:64 * t[1] + 64].sum())
         sl = np.s_[64 * ty:64 * ty + 64, 64 * tx:64 * tx + 64]
-        xs.append(ref.tile_input(st["warped"][sl], st["mask"][sl], st["zt"][sl], d[sl], cfg.near))
+        xs.append(ref.tile_input(st["out"][sl], st["mask"][sl], st["zt"][sl], d[sl], cfg.near))
         gts.append(cr[sl][..., :3])
         holes.append(st["mask"][sl])
     return np.stack(xs), np.stack(gts), np.stack(holes)

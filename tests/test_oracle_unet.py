@@ -154,14 +154,15 @@ def test_compose_keeps_reached_pixels_and_rounds_the_holes():
 
 
 def test_input_channels_of_a_tile():
-    warped = np.full((8, 8, 4), 51, np.uint8)
+    color = np.full((8, 8, 4), 51, np.uint8)
+    color[:, 5:, :3] = 102  # the Patcher's fill at the holes is an input too
     mask = np.zeros((8, 8), np.uint8)
     mask[:, 5:] = 1
     zt = np.full((8, 8), 2.0, np.float32)
     zt[:, 5:] = np.inf
     zsrc = np.full((8, 8), 4.0, np.float32)
-    x = unet.tile_input(warped, mask, zt, zsrc, near=0.5)
-    assert np.allclose(x[0:3, :, :5], 0.2) and (x[0:3, :, 5:] == 0).all()
+    x = unet.tile_input(color, mask, zt, zsrc, near=0.5)
+    assert np.allclose(x[0:3, :, :5], 0.2) and np.allclose(x[0:3, :, 5:], 0.4)
     assert (x[3] == mask).all()
     assert np.allclose(x[4, :, :5], 0.25) and (x[4, :, 5:] == 0).all()
     assert np.allclose(x[5], 0.125)
