@@ -12,7 +12,10 @@
 // mbarriers between them (4 stages).  The epilogue reads the accumulators with
 // tcgen05.ld, adds the bias, applies ReLU, rounds to BF16 and stores NHWC at a channel
 // offset of a wider buffer (so a decoder's concatenation is written in place), or, for
-// the layer below a decoder level, to the 2 x 2 pixels of the nearest upsampling.
+// the layer below a decoder level, to the 2 x 2 pixels of the nearest upsampling.  One
+// CTA per 128-pixel tile: with 128 threads and 4 stages, several CTAs share an SM and
+// keep about 20 stages of copies in flight there (the narrow layers stream their
+// activations from L2 once per tap).
 //
 // Every wait on an mbarrier has a deadline (1 s of %globaltimer): a wait that runs out
 // records kUnetTimeout in a status word, the kernel waits (again bounded) for the copies
@@ -311,203 +314,6 @@ __global__ void __launch_bounds__(128, 1)
     }
 }
 
-// Wait with an abort flag: false when `abort` was raised or `deadline` passed.
-__device__ __forceinline__ bool mbar_wait_or_abort(uint64_t* bar, uint32_t parity, volatile int* abort)
-{
-    const uint64_t deadline = globaltimer() + kWaitNs;
-    while (!mbar_try_wait(bar, parity)) {
-        if (*abort) return false;
-        if (globaltimer() > deadline) {
-            atomicOr(&g_unet_status, kUnetTimeout);
-            *abort = 1;
-            return false;
-        }
-    }
-    return true;
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
-// The persistent form of the convolution: each CTA walks the 128-pixel tiles tile =
-// blockIdx.x, + gridDim.x, ... with three roles.  Warp 0 (one lane) streams the copies of
-// every K step of every tile through the 4-stage ring; warp 1 (one lane) issues the MMAs
-// of a tile into one of two accumulators in tensor memory and commits it; warps 2-5 read
-// an accumulator back (warp w takes TMEM lanes 32 (w % 4) ..), write the tile's output and
-// hand the accumulator back.  So the output of one tile is written while the MMAs of the
-// next run, and a CTA's set-up is paid once for many tiles.  Every wait is bounded; a
-// wait that runs out raises the CTA's abort flag, which every role checks, and records
-// kUnetTimeout.
-__global__ void __launch_bounds__(192, 1)
-    conv3x3_tcp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const ConvArgs a,
-                int ntiles)
-{
-    extern __shared__ unsigned char smem_raw[];
-    unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
-                                                           ~static_cast<uintptr_t>(1023));
-    const int b_bytes = a.Cout * kKc * 2;
-    const int stage_bytes = kABytes + ((b_bytes + 1023) & ~1023);
-    uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * stage_bytes);
-    uint64_t* empty = full + kStages;
-    uint64_t* accf = empty + kStages;  // accumulator b holds a finished tile
-    uint64_t* acce = accf + 2;         // accumulator b was read back
-    uint64_t* mdone = acce + 2;        // every MMA this CTA issued has completed
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(mdone + 1);
-    volatile int* abort = reinterpret_cast<volatile int*>(tslot + 1);
-    volatile int* counts = abort + 1;  // [0] copies issued, [1] stages consumed by MMAs
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-
-    if (threadIdx.x == 0) {
-        for (int s = 0; s < kStages; ++s) {
-            mbar_init(&full[s], 1);
-            mbar_init(&empty[s], 1);
-        }
-        for (int b = 0; b < 2; ++b) {
-            mbar_init(&accf[b], 1);
-            mbar_init(&acce[b], 4);
-        }
-        mbar_init(mdone, 1);
-        *abort = 0;
-        counts[0] = 0;
-        counts[1] = 0;
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
-                     "r"(2 * a.ncols)
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-    }
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    const uint32_t tmem = *tslot;
-    const int cb_n = a.Cin / kKc;
-    const int nk = 9 * cb_n;
-    const int hw = a.H * a.W;
-    const int live = a.count ? *a.count : 0x7fffffff;  // tiles at or after `live` are skipped
-
-    if (warp == 0) {
-        if (lane == 0) {  // copies
-            int kk = 0;
-            for (int tile = blockIdx.x; tile < ntiles && !*abort; tile += gridDim.x) {
-                const int p0 = tile * kTileM, n0 = p0 / hw, y0 = (p0 - n0 * hw) / a.W;
-                if (n0 >= live) continue;
-                for (int k = 0; k < nk; ++k, ++kk) {
-                    const int s = kk % kStages;
-                    if (!mbar_wait_or_abort(&empty[s], ((kk / kStages) & 1) ^ 1, abort)) break;
-                    const int tap = k / cb_n, cb = k - tap * cb_n;
-                    const int dy = tap / 3, dx = tap - 3 * (tap / 3);
-                    unsigned char* sa = smem + s * stage_bytes;
-                    mbar_expect_tx(&full[s], (uint32_t)(kABytes + b_bytes));
-                    tma_load_4d(sa, &tmA, &full[s], cb * kKc, dx - 1, y0 + dy - 1, n0);
-                    tma_load_2d(sa + kABytes, &tmB, &full[s], tap * a.Cin + cb * kKc, 0);
-                    counts[0] = kk + 1;
-                }
-            }
-        }
-    } else if (warp == 1) {
-        if (lane == 0) {  // MMAs
-            const uint32_t idesc = idesc_bf16(a.Cout);
-            int kk = 0, it = 0;
-            for (int tile = blockIdx.x; tile < ntiles && !*abort; tile += gridDim.x, ++it) {
-                const int n0 = (tile * kTileM) / hw;
-                if (n0 >= live) {
-                    --it;
-                    continue;
-                }
-                const int b = it & 1;
-                if (!mbar_wait_or_abort(&acce[b], ((it >> 1) & 1) ^ 1, abort)) break;
-                tc_fence_after();
-                const uint32_t d = tmem + (uint32_t)(b * a.ncols);
-                bool ok = true;
-                for (int k = 0; k < nk; ++k, ++kk) {
-                    const int s = kk % kStages;
-                    if (!mbar_wait_or_abort(&full[s], (kk / kStages) & 1, abort)) {
-                        ok = false;
-                        break;
-                    }
-                    tc_fence_after();
-                    const uint32_t sa = smem_u32(smem + s * stage_bytes), sb = sa + kABytes;
-                    mma_bf16(d, desc_sw64(sa), desc_sw64(sb), idesc, k > 0 ? 1u : 0u);
-                    mma_bf16(d, desc_sw64(sa + 32), desc_sw64(sb + 32), idesc, 1u);
-                    mma_commit(&empty[s]);
-                    counts[1] = kk + 1;
-                }
-                if (!ok) break;
-                mma_commit(&accf[b]);
-            }
-            // before the tensor memory can be freed, every MMA issued above must be done
-            mma_commit(mdone);
-            if (!mbar_wait(mdone, 0, globaltimer() + kWaitNs)) atomicOr(&g_unet_status, kUnetTimeout);
-        }
-    } else {  // epilogue: warps 2..5
-        const int q = warp & 3;  // TMEM lane quadrant this warp may read
-        int it = 0;
-        for (int tile = blockIdx.x; tile < ntiles && !*abort; tile += gridDim.x, ++it) {
-            const int p0 = tile * kTileM;
-            if (p0 / hw >= live) {
-                --it;
-                continue;
-            }
-            const int b = it & 1;
-            if (!mbar_wait_or_abort(&accf[b], (it >> 1) & 1, abort)) break;
-            tc_fence_after();
-            const int p = p0 + q * 32 + lane;  // this thread's pixel = its TMEM lane
-            const int n = p / hw, rem = p - n * hw, yy = rem / a.W, xx = rem - (rem / a.W) * a.W;
-            for (int c0 = 0; c0 < a.Cout; c0 += 32) {
-                uint32_t r[32];
-                tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * a.ncols + c0), r);
-                uint4 v4[4];
-                uint32_t* qw = reinterpret_cast<uint32_t*>(v4);
-#pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    float v0 = __fadd_rn(__uint_as_float(r[2 * i]), __ldg(a.bias + c0 + 2 * i));
-                    float v1 = __fadd_rn(__uint_as_float(r[2 * i + 1]), __ldg(a.bias + c0 + 2 * i + 1));
-                    if (a.relu) {
-                        v0 = fmaxf(v0, 0.0f);
-                        v1 = fmaxf(v1, 0.0f);
-                    }
-                    qw[i] = pack_bf16x2(v0, v1);
-                }
-                if (!a.upsample) {
-                    uint4* dst = reinterpret_cast<uint4*>(a.y + ((size_t)p * a.y_cstride + a.y_coff + c0));
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) dst[i] = v4[i];
-                } else {
-                    const int W2 = 2 * a.W, H2 = 2 * a.H;
-#pragma unroll
-                    for (int ab = 0; ab < 4; ++ab) {
-                        const size_t op = ((size_t)n * H2 + (2 * yy + (ab >> 1))) * W2 + (2 * xx + (ab & 1));
-                        uint4* dst = reinterpret_cast<uint4*>(a.y + (op * a.y_cstride + a.y_coff + c0));
-#pragma unroll
-                        for (int i = 0; i < 4; ++i) dst[i] = v4[i];
-                    }
-                }
-            }
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&acce[b]);
-        }
-    }
-    __syncwarp();
-    tc_fence_before();
-    __syncthreads();
-    if (threadIdx.x == 0 && *abort) {  // copies still in flight after an abort: wait for them (bounded)
-        const uint64_t d2 = globaltimer() + kWaitNs;
-        for (int k = counts[1]; k < counts[0]; ++k)
-            if (!mbar_wait(&full[k % kStages], (k / kStages) & 1, d2)) break;
-    }
-    __syncthreads();
-    if (warp == 0) {
-        tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * a.ncols)
-                     : "memory");
-    }
-}
-
 // Driver entry point for tensor-map encoding, looked up once through the runtime (no
 // link against the driver library).
 using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -533,27 +339,7 @@ size_t conv_smem_bytes(int cout)
 {
     const int b_bytes = cout * kKc * 2;
     const int stage = kABytes + ((b_bytes + 1023) & ~1023);
-    return 1024 + (size_t)kStages * stage + (2 * kStages + 5) * 8 + 32;
-}
-
-// CTAs of the persistent convolution per SM: what shared memory allows, and at most
-// 512 / (2 ncols) so that every resident CTA's two accumulators fit the 512 TMEM columns
-// (an allocation never waits for another CTA).
-int conv_ctas_per_sm(int cout)
-{
-    static int cache[5] = {0, 0, 0, 0, 0};
-    const int idx = cout == 32 ? 0 : cout == 64 ? 1 : cout == 128 ? 2 : 3;
-    if (!cache[idx]) {
-        int occ = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, conv3x3_tcp, 192, conv_smem_bytes(cout)) !=
-                cudaSuccess ||
-            occ < 1) {
-            cudaGetLastError();
-            occ = 1;
-        }
-        cache[idx] = std::max(1, std::min(occ, 512 / (2 * std::max(cout, 32))));
-    }
-    return cache[idx];
+    return 1024 + (size_t)kStages * stage + (2 * kStages + 1) * 8 + 16;
 }
 
 }  // namespace
@@ -629,20 +415,14 @@ cudaError_t unet_conv3x3(const void* x, int T, int H, int W, int Cin, const void
     a.ncols = Cout < 32 ? 32 : Cout;
     a.count = count;
     const size_t smem = conv_smem_bytes(Cout);
-    static int configured_dev = -1;
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return cudaErrorInvalidDevice;
-    if (configured_dev != dev) {
+    static bool configured = false;
+    if (!configured) {
         const cudaError_t e =
-            cudaFuncSetAttribute(conv3x3_tcp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)conv_smem_bytes(256));
+            cudaFuncSetAttribute(conv3x3_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)conv_smem_bytes(256));
         if (e != cudaSuccess) return e;
-        configured_dev = dev;
+        configured = true;
     }
-    static int sms = 0;
-    if (!sms && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return cudaErrorUnknown;
-    const long long ntiles = pixels / kTileM;
-    const long long grid = std::min<long long>(ntiles, (long long)sms * conv_ctas_per_sm(Cout));
-    conv3x3_tcp<<<(unsigned)grid, 192, smem, stream>>>(ta, tb, a, (int)ntiles);
+    conv3x3_tc<<<(unsigned)(pixels / kTileM), 128, smem, stream>>>(ta, tb, a);
     return cudaGetLastError();
 }
 
