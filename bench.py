@@ -62,6 +62,8 @@ def parse():
     p.add_argument("--imbuffer-div", type=int, default=4, help="imbuffer workload: source pixels per cell")
     p.add_argument("--no-interpolate", action="store_true", help="imbuffer workload: no linear interpolation")
     p.add_argument("--no-tune", action="store_true", help="batch workload: skip the band-height autotuner")
+    p.add_argument("--tiles", type=int, default=0,
+                   help="inpaint workload: tiles per network step (0: every tile of a 1832x1920 frame, 870)")
     p.add_argument("--streams", type=int, default=4,
                    help="streams the steps are issued on, round-robin (frames overlap on the GPU)")
     return p.parse_args()
@@ -532,6 +534,23 @@ def run_serve(args):
     sat_frames = sum(len(st["lat"]) for st in streams)
     sat_px = sum(len(st["lat"]) * st["cfg"].w * st["cfg"].h for st in streams)
     srv.drain(60000)
+    # saturation again with the server's own feeder thread (no host loop in the way)
+    for r in srv.poll(1 << 16):
+        pass
+    for st in streams:
+        srv.feed(st["id"], st["pool"], nframes=1 << 40, hz=0.0)
+    feed_n, feed_px = 0, 0
+    t_f0 = time.perf_counter()
+    while time.perf_counter() - t_f0 < 2.0:
+        for r in srv.poll(1 << 16):
+            st = streams[r.stream]
+            feed_n += 1
+            feed_px += st["cfg"].w * st["cfg"].h
+        time.sleep(0.001)
+    feed_secs = time.perf_counter() - t_f0
+    srv.feed_stop()
+    srv.drain(60000)
+    srv.poll(1 << 16)
     srv.set_inpainter(None)  # the fallback: learned streams keep the paper's fill
     fb_secs = run(max(2.0, args.serve_seconds), paced=True)
     fallback = report(fb_secs)
@@ -550,6 +569,9 @@ def run_serve(args):
         "fallback_streams": fallback,
         "saturation": {"frames_per_s": round(sat_frames / sat_secs, 1), "mpix_per_s": round(sat_px / sat_secs / 1e6, 1),
                        "what": "every stream resubmits as soon as one of its 3 slots frees up (host loop, one thread)"},
+        "saturation_feeder": {"frames_per_s": round(feed_n / feed_secs, 1), "mpix_per_s": round(feed_px / feed_secs / 1e6, 1),
+                              "what": "the same with the server's feeder thread copying pose frames into free slots "
+                                      "(yoro_server_feed, no host loop); learned streams repainted"},
     }), flush=True)
 
 
@@ -571,7 +593,7 @@ def run_inpaint(args):
     else:
         params, weights_kind = W.init_params(1), "initial (seeded He-normal)"
     ntx, nty = (cfg.w + 63) // 64, (cfg.h + 63) // 64
-    T = ntx * nty
+    T = args.tiles if args.tiles > 0 else ntx * nty
     net = un.Inpainter(params, max_tiles=T, max_w=cfg.w, max_h=cfg.h)
     g = torch.Generator(device="cuda").manual_seed(5)
     x = torch.zeros((T, 64, 64, 32), dtype=torch.bfloat16, device="cuda")
@@ -619,8 +641,8 @@ def run_inpaint(args):
         "value": round(tflops, 2), "unit": "TFLOP/s", "n_gpus": 1, "steps": steps, "warmup": args.warmup,
         "ms_per_step": round(ms, 4), "higher_is_better": True, "dtype": "bf16 (fp32 accumulate)",
         "data": "synthetic", "weights": weights_kind,
-        "config": {"workload": f"every 64x64 tile of a 1832x1920 frame ({T} tiles per step), 4-level U-Net "
-                               "32/64/128/256", "flops_per_tile": W.flops_per_tile(), "tiles": T},
+        "config": {"workload": f"{T} 64x64 tiles per step ({ntx * nty}: every tile of a 1832x1920 frame), 4-level "
+                               "U-Net 32/64/128/256", "flops_per_tile": W.flops_per_tile(), "tiles": T},
         "roofline": {"bound": "tensor", "achieved": round(tflops, 2), "peak": peak, "unit": "TFLOP/s",
                      "frac": round(tflops / peak, 4), "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst)"},
         "frame_path_ms": {"p50": round(lat[len(lat) // 2], 3), "p99": round(lat[int(0.99 * (len(lat) - 1))], 3),

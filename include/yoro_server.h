@@ -98,6 +98,21 @@ yoro_status yoro_server_pause(yoro_server s, int paused);
  */
 int yoro_server_cancel(yoro_server s, int stream);
 
+/*
+ * Feed a stream from device memory without a host loop: the server's feeder thread
+ * copies source frame i % nsrc (colors[i]: w*h*4 bytes, depths[i]: w*h floats, device
+ * pointers the caller keeps valid until the job ends) into a free slot of the stream and
+ * submits it, nframes times, with tags tag0, tag0 + 1, ...; hz > 0 paces the frames at
+ * that rate, hz = 0 sends each as soon as a slot is free.  Returns at once; completions
+ * arrive through yoro_server_poll as for yoro_server_submit.  Jobs of several streams run
+ * side by side.  A stream fed this way must not also be submitted to by the caller.
+ */
+yoro_status yoro_server_feed(yoro_server s, int stream, const void* const* colors, const float* const* depths,
+                             int nsrc, long long nframes, float hz, unsigned long long tag0);
+
+/* End every feeding job (frames already submitted complete normally). */
+yoro_status yoro_server_feed_stop(yoro_server s);
+
 /* Remove a stream: waits until its submitted frames are done, then frees its slots.
  * Its completions stay available to yoro_server_poll. */
 yoro_status yoro_server_leave(yoro_server s, int stream);

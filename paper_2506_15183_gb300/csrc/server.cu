@@ -10,7 +10,9 @@
 // an inpainter (or for a frame larger than it takes) they keep the paper's fill.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <chrono>
+#include <cmath>
 #include <condition_variable>
 #include <cstdint>
 #include <deque>
@@ -65,13 +67,29 @@ struct Request {
     unsigned long long tag;
     long long submit_ns;
     int inpainted;
+    int learned;  // the frame's stream repaints holes with the inpainter
+};
+
+// A feeding job (yoro_server_feed): source frames copied into the stream's free slots
+// and submitted by the server's feeder thread.
+struct FeedJob {
+    int stream;
+    std::vector<const void*> colors;
+    std::vector<const float*> depths;
+    long long remaining;
+    long long next;          // index of the next source frame (cyclic)
+    double period_ns;        // 0: as fast as slots free up
+    long long due_ns;        // when the next frame may go (paced jobs)
+    unsigned long long tag;  // tag of the next frame
 };
 
 struct Batch {
     std::vector<Request> req;
-    cudaEvent_t done = nullptr;
+    cudaEvent_t synth = nullptr;  // the batched synthesis is done (plain frames complete here)
+    cudaEvent_t done = nullptr;   // the learned frames' inpainting is done too
     long long launch_ns = 0;
     yoro_status status = YORO_OK;
+    bool any_learned = false;
 };
 
 constexpr int kMaxSlots = 64;
@@ -95,16 +113,26 @@ struct yoro_server_ctx {
     yoro_unet inpainter = nullptr;
     Batch ring[kInFlight];
     std::thread worker;
+    // feeder
+    std::vector<FeedJob> jobs;
+    std::thread feeder;
+    bool feeder_started = false;
+    cudaStream_t fs = nullptr;
 
     void run();
-    void complete(Batch& b, long long t_done);
+    void feed_loop();
+    void complete(Batch& b, long long t_done, int which);
 };
 
-void yoro_server_ctx::complete(Batch& b, long long t_done)
+// which: 0 the plain frames of the batch, 1 the learned ones, 2 all; the batch's request
+// list is cleared once its last frames are reported.
+void yoro_server_ctx::complete(Batch& b, long long t_done, int which)
 {
     {
         std::lock_guard<std::mutex> lk(mu);
         for (const Request& r : b.req) {
+            const bool learned_frame = r.learned != 0;
+            if ((which == 0 && learned_frame) || (which == 1 && !learned_frame)) continue;
             yoro_completion c;
             c.stream = r.stream;
             c.slot = r.slot;
@@ -121,7 +149,7 @@ void yoro_server_ctx::complete(Batch& b, long long t_done)
             --st.pending;
             --outstanding;
         }
-        b.req.clear();
+        if (which != 0) b.req.clear();
     }
     cv_done.notify_all();
 }
@@ -168,6 +196,7 @@ void yoro_server_ctx::run()
                     frames.push_back(f);
                     zts.push_back(st.learned ? sl.zt : nullptr);
                     b.req.push_back(r);
+                    b.req.back().learned = st.learned ? 1 : 0;
                 }
             }
             if (!b.req.empty()) {
@@ -176,6 +205,8 @@ void yoro_server_ctx::run()
                 for (float* z : zts) any_learned = any_learned || z != nullptr;
                 b.status = (yoro_status)yoro::synthesize_batch_zt((int)frames.size(), frames.data(),
                                                                   any_learned ? zts.data() : nullptr, cs);
+                b.any_learned = any_learned;
+                if (b.status == YORO_OK && cudaEventRecord(b.synth, cs) != cudaSuccess) b.status = YORO_ECUDA;
                 // learned inpainting of those frames, one after another on the same stream
                 for (size_t i = 0; i < b.req.size(); ++i) {
                     b.req[i].inpainted = 0;
@@ -193,11 +224,98 @@ void yoro_server_ctx::run()
         if (count == 0) continue;
         if (launched && count < kInFlight) continue;  // gather the next batch while this one runs
         Batch& old = ring[head];
+        bool plain_reported = false;
+        if (old.any_learned && old.status == YORO_OK) {  // plain frames leave when the synthesis is done
+            if (cudaEventSynchronize(old.synth) != cudaSuccess) old.status = YORO_ECUDA;
+            if (old.status == YORO_OK) {
+                complete(old, now_ns(), 0);
+                plain_reported = true;
+            }
+        }
         if (old.status == YORO_OK && cudaEventSynchronize(old.done) != cudaSuccess) old.status = YORO_ECUDA;
         if (old.status != YORO_OK) cudaGetLastError();
-        complete(old, now_ns());
+        complete(old, now_ns(), plain_reported ? 1 : 2);
         head = (head + 1) % kInFlight;
         --count;
+    }
+}
+
+void yoro_server_ctx::feed_loop()
+{
+    cudaSetDevice(device);
+    std::unique_lock<std::mutex> lk(mu);
+    for (;;) {
+        if (stop) break;
+        const long long now = now_ns();
+        long long wake = -1;  // earliest due time of a paced job waiting for its time
+        bool progressed = false;
+        for (size_t j = 0; j < jobs.size(); ++j) {
+            FeedJob& jb = jobs[j];
+            if (jb.remaining <= 0) continue;
+            Stream& st = streams[jb.stream];
+            if (!st.live) {
+                jb.remaining = 0;
+                continue;
+            }
+            if (jb.period_ns > 0 && now < jb.due_ns) {
+                wake = wake < 0 ? jb.due_ns : std::min(wake, jb.due_ns);
+                continue;
+            }
+            int k = -1;
+            for (int i = 0; i < (int)st.slots.size(); ++i)
+                if (!st.slots[i].in_flight) {
+                    k = i;
+                    break;
+                }
+            if (k < 0) continue;  // every slot busy: a completion wakes us
+            // Reserve the slot and count the frame as pending before the lock is dropped
+            // (leave() then waits for it); take plain values only: admit() or feed() may
+            // grow the vectors while the copy runs.
+            st.slots[k].in_flight = true;
+            ++st.pending;
+            ++outstanding;
+            void* dst_c = st.slots[k].color;
+            float* dst_d = st.slots[k].depth;
+            const size_t n = (size_t)st.w * st.h;
+            const void* c = jb.colors[jb.next % jb.colors.size()];
+            const float* d = jb.depths[jb.next % jb.depths.size()];
+            const int sid = jb.stream;
+            const unsigned long long tag = jb.tag++;
+            ++jb.next;
+            --jb.remaining;
+            if (jb.period_ns > 0) jb.due_ns += (long long)jb.period_ns;
+            lk.unlock();
+            const bool ok = cudaMemcpyAsync(dst_c, c, 4 * n, cudaMemcpyDeviceToDevice, fs) == cudaSuccess &&
+                            cudaMemcpyAsync(dst_d, d, 4 * n, cudaMemcpyDeviceToDevice, fs) == cudaSuccess &&
+                            cudaStreamSynchronize(fs) == cudaSuccess;
+            lk.lock();
+            if (!ok) {
+                cudaGetLastError();
+                streams[sid].slots[k].in_flight = false;
+                --streams[sid].pending;
+                --outstanding;
+                cv_done.notify_all();
+                continue;
+            }
+            pending.push_back(Request{sid, k, tag, now_ns(), 0, 0});
+            cv_work.notify_one();
+            progressed = true;
+        }
+        if (progressed) continue;
+        bool any = false;
+        for (const FeedJob& jb : jobs) any = any || jb.remaining > 0;
+        if (!any) {
+            cv_done.wait(lk, [&] {
+                if (stop) return true;
+                for (const FeedJob& jb : jobs)
+                    if (jb.remaining > 0) return true;
+                return false;
+            });
+        } else if (wake >= 0) {
+            cv_done.wait_for(lk, std::chrono::nanoseconds(std::max<long long>(wake - now_ns(), 0)));
+        } else {
+            cv_done.wait_for(lk, std::chrono::milliseconds(5));
+        }
     }
 }
 
@@ -220,11 +338,15 @@ yoro_server yoro_server_create(size_t memory_budget_bytes, int max_batch)
               cudaStreamCreateWithFlags(&s->cs, cudaStreamNonBlocking) == cudaSuccess;
     for (int i = 0; ok && i < kInFlight; ++i)
         ok = cudaEventCreateWithFlags(&s->ring[i].done, cudaEventBlockingSync | cudaEventDisableTiming) ==
-             cudaSuccess;
+                 cudaSuccess &&
+             cudaEventCreateWithFlags(&s->ring[i].synth, cudaEventBlockingSync | cudaEventDisableTiming) ==
+                 cudaSuccess;
     if (!ok) {
         cudaGetLastError();
-        for (Batch& b : s->ring)
+        for (Batch& b : s->ring) {
             if (b.done) cudaEventDestroy(b.done);
+            if (b.synth) cudaEventDestroy(b.synth);
+        }
         if (s->cs) cudaStreamDestroy(s->cs);
         delete s;
         yoro::set_last_create_error(YORO_ECUDA);
@@ -233,7 +355,10 @@ yoro_server yoro_server_create(size_t memory_budget_bytes, int max_batch)
     try {
         s->worker = std::thread([s] { s->run(); });
     } catch (...) {
-        for (Batch& b : s->ring) cudaEventDestroy(b.done);
+        for (Batch& b : s->ring) {
+            cudaEventDestroy(b.done);
+            cudaEventDestroy(b.synth);
+        }
         cudaStreamDestroy(s->cs);
         delete s;
         yoro::set_last_create_error(YORO_ENOMEM);
@@ -249,13 +374,20 @@ void yoro_server_destroy(yoro_server s)
     {
         std::lock_guard<std::mutex> lk(s->mu);
         s->stop = true;
+        for (FeedJob& jb : s->jobs) jb.remaining = 0;
     }
     s->cv_work.notify_all();
+    s->cv_done.notify_all();
+    if (s->feeder.joinable()) s->feeder.join();
+    if (s->fs) cudaStreamDestroy(s->fs);
     if (s->worker.joinable()) s->worker.join();
     cudaStreamSynchronize(s->cs);
     for (Stream& st : s->streams)
         if (st.block) cudaFree(st.block);
-    for (Batch& b : s->ring) cudaEventDestroy(b.done);
+    for (Batch& b : s->ring) {
+        cudaEventDestroy(b.done);
+        cudaEventDestroy(b.synth);
+    }
     cudaStreamDestroy(s->cs);
     delete s;
 }
@@ -370,7 +502,7 @@ yoro_status yoro_server_submit(yoro_server s, int stream, int slot, unsigned lon
         st.slots[slot].in_flight = true;
         ++st.pending;
         ++s->outstanding;
-        s->pending.push_back(Request{stream, slot, tag, now_ns(), 0});
+        s->pending.push_back(Request{stream, slot, tag, now_ns(), 0, 0});
     }
     s->cv_work.notify_one();
     return YORO_OK;
@@ -395,6 +527,54 @@ yoro_status yoro_server_drain(yoro_server s, int timeout_ms)
     const bool ok = s->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms < 0 ? 0 : timeout_ms),
                                         [&] { return s->outstanding == 0; });
     return ok ? YORO_OK : YORO_ETIMEOUT;
+}
+
+yoro_status yoro_server_feed(yoro_server s, int stream, const void* const* colors, const float* const* depths,
+                             int nsrc, long long nframes, float hz, unsigned long long tag0)
+{
+    if (!s || !colors || !depths || nsrc < 1 || nframes < 0 || !(hz >= 0.0f) || !std::isfinite(hz)) return YORO_EINVAL;
+    for (int i = 0; i < nsrc; ++i)
+        if (!colors[i] || !depths[i]) return YORO_EINVAL;
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (stream < 0 || stream >= (int)s->streams.size() || !s->streams[stream].live) return YORO_EINVAL;
+    if (!s->feeder_started) {
+        if (cudaStreamCreateWithFlags(&s->fs, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            return YORO_ECUDA;
+        }
+        try {
+            s->feeder = std::thread([s] { s->feed_loop(); });
+        } catch (...) {
+            cudaStreamDestroy(s->fs);
+            s->fs = nullptr;
+            return YORO_ENOMEM;
+        }
+        s->feeder_started = true;
+    }
+    FeedJob jb;
+    jb.stream = stream;
+    jb.colors.assign(colors, colors + nsrc);
+    jb.depths.assign(depths, depths + nsrc);
+    jb.remaining = nframes;
+    jb.next = 0;
+    jb.period_ns = hz > 0.0f ? 1e9 / (double)hz : 0.0;
+    jb.due_ns = now_ns();
+    jb.tag = tag0;
+    s->jobs.push_back(std::move(jb));
+    s->cv_done.notify_all();
+    return YORO_OK;
+}
+
+yoro_status yoro_server_feed_stop(yoro_server s)
+{
+    if (!s) return YORO_EINVAL;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        for (FeedJob& jb : s->jobs) jb.remaining = 0;
+        s->jobs.clear();
+    }
+    s->cv_done.notify_all();
+    return YORO_OK;
 }
 
 yoro_status yoro_server_set_inpainter(yoro_server s, yoro_unet u)

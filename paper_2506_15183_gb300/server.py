@@ -50,6 +50,11 @@ def _lib():
         lib.yoro_server_pause.restype = I
         lib.yoro_server_cancel.argtypes = [P, I]
         lib.yoro_server_cancel.restype = I
+        lib.yoro_server_feed.argtypes = [P, I, ctypes.POINTER(P), ctypes.POINTER(P), I, ctypes.c_longlong, F,
+                                         ctypes.c_ulonglong]
+        lib.yoro_server_feed.restype = I
+        lib.yoro_server_feed_stop.argtypes = [P]
+        lib.yoro_server_feed_stop.restype = I
         lib._server_typed = True
     return lib
 
@@ -131,6 +136,19 @@ class Server:
         if n < 0:
             raise YoroError(-n, "yoro_server_cancel")
         return n
+
+    def feed(self, stream: int, frames, nframes: int, hz: float = 0.0, tag0: int = 0) -> None:
+        """The server's feeder copies frames[i % len(frames)] = (color, depth) device tensors
+        into the stream's free slots and submits them, nframes times (hz > 0: paced)."""
+        n = len(frames)
+        cols = (ctypes.c_void_p * n)(*[c.data_ptr() for c, _ in frames])
+        deps = (ctypes.c_void_p * n)(*[d.data_ptr() for _, d in frames])
+        st = _lib().yoro_server_feed(self._s, int(stream), cols, deps, n, int(nframes), float(hz), int(tag0))
+        if st != 0:
+            raise YoroError(st, "yoro_server_feed")
+
+    def feed_stop(self) -> None:
+        _lib().yoro_server_feed_stop(self._s)
 
     def memory_used(self) -> int:
         return int(_lib().yoro_server_memory_used(self._s))

@@ -284,3 +284,40 @@ def test_an_oversized_frame_is_refused_at_admission(srv):
     assert e.value.code == 6  # YORO_ETOOBIG
     assert s.memory_used() == 0
     s.close()
+
+
+def test_the_feeder_submits_from_device_sources(srv):
+    """yoro_server_feed: the server's own thread copies source frames into free slots and
+    submits them, unpaced and paced; every frame gets the oracle's bytes for its source."""
+    frames = [_small(3), _small(5)]
+    cfg = frames[0][0]
+    s = srv.Server(1 << 30, max_batch=8)
+    a = s.admit(**cfg.camera(), slots=2)
+    src = [(torch.from_numpy(c).cuda(), torch.from_numpy(d).cuda()) for _, c, d in frames]
+    torch.cuda.synchronize()
+    s.feed(a, src, nframes=6, tag0=100)
+    s.drain()
+    got = []
+    while len(got) < 6:
+        got += s.poll()
+        s.drain()
+    assert sorted(r.tag for r in got) == list(range(100, 106)) and all(r.status == 0 for r in got)
+    # the last frame sent (tag 105) was source 1; its slot holds that frame's result
+    last = max(got, key=lambda r: r.tag)
+    fcfg, fc, fd = frames[1]
+    ref = oracle.synthesize(fc, fd, fcfg.fx, fcfg.fy, fcfg.cx, fcfg.cy, fcfg.ipd, fcfg.near, fcfg.far)
+    assert np.array_equal(s.slot(a, last.slot)[2].cpu().numpy(), ref[0])
+    # paced at 200 Hz: submissions at least ~5 ms apart
+    s.feed(a, src, nframes=5, hz=200.0, tag0=200)
+    import time
+
+    t0 = time.time()
+    paced = []
+    while len(paced) < 5 and time.time() - t0 < 10:
+        paced += s.poll()
+        time.sleep(0.002)
+    assert sorted(r.tag for r in paced) == list(range(200, 205))
+    sub = sorted(r.submit_ns for r in paced)
+    assert min(b - a_ for a_, b in zip(sub, sub[1:])) >= 4_000_000
+    s.feed_stop()
+    s.close()
