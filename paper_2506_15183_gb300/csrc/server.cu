@@ -1,13 +1,16 @@
 // Serving loop: admitted streams with resident frame slots, continuous batching by a
 // scheduler thread.  Contract in include/yoro_server.h.
 //
-// The scheduler keeps up to two batches in flight on its own CUDA stream: it launches
+// The scheduler keeps up to four batches in flight on its own CUDA stream: it launches
 // whatever is pending as one batched synthesis, and while that runs, gathers the frames
 // submitted meanwhile into the next launch; it then waits (a blocking-sync CUDA event, so
 // the thread sleeps) for the older batch and reports its frames complete.  Frames of
 // streams admitted with learned inpainting also get their warped depth from the batch,
-// and then, on the same CUDA stream, the server's inpainter repaints their holes; without
-// an inpainter (or for a frame larger than it takes) they keep the paper's fill.
+// and then, on a second CUDA stream ordered after the synthesis by an event, the server's
+// inpainter repaints their holes; a host function enqueued after them reports those
+// frames, so a batch retires, and the scheduler moves on, as soon as its synthesis is
+// done.  Without an inpainter (or for a frame larger than it takes) learned frames keep
+// the paper's fill and complete with the batch.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -90,10 +93,13 @@ struct Batch {
     long long launch_ns = 0;
     yoro_status status = YORO_OK;
     bool any_learned = false;
+    int frames = 0;  // frames launched in this batch (learned ones included)
 };
 
+struct LearnedDone;  // learned frames of one batch, reported by a host function on the inpainting stream
+
 constexpr int kMaxSlots = 64;
-constexpr int kInFlight = 2;
+constexpr int kInFlight = 4;
 
 }  // namespace
 
@@ -101,7 +107,9 @@ struct yoro_server_ctx {
     int device = 0;
     size_t budget = 0, used = 0;
     int max_batch = 0;
-    cudaStream_t cs = nullptr;
+    cudaStream_t cs = nullptr;  // synthesis
+    cudaStream_t ci = nullptr;  // learned inpainting, after each batch's synthesis (its own queue,
+                                // so the next batch's synthesis does not wait behind it)
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
     std::deque<Request> pending;
@@ -122,7 +130,53 @@ struct yoro_server_ctx {
     void run();
     void feed_loop();
     void complete(Batch& b, long long t_done, int which);
+    void report(const std::vector<Request>& reqs, long long launch_ns, int batch_frames, yoro_status status,
+                long long t_done);
 };
+
+namespace {
+struct LearnedDone {
+    yoro_server_ctx* server;
+    std::vector<Request> req;
+    long long launch_ns;
+    int batch_frames;
+};
+
+// Runs on the CUDA runtime's thread once the inpainting enqueued before it is done; it
+// touches host state only (no CUDA call is allowed here).
+void CUDART_CB learned_done(void* p)
+{
+    LearnedDone* d = static_cast<LearnedDone*>(p);
+    d->server->report(d->req, d->launch_ns, d->batch_frames, YORO_OK, now_ns());
+    delete d;
+}
+}  // namespace
+
+void yoro_server_ctx::report(const std::vector<Request>& reqs, long long launch_ns, int batch_frames,
+                             yoro_status status, long long t_done)
+{
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        for (const Request& r : reqs) {
+            yoro_completion c;
+            c.stream = r.stream;
+            c.slot = r.slot;
+            c.tag = r.tag;
+            c.submit_ns = r.submit_ns;
+            c.launch_ns = launch_ns;
+            c.done_ns = t_done;
+            c.batch_frames = batch_frames;
+            c.status = status;
+            c.inpainted = status == YORO_OK ? r.inpainted : 0;
+            done.push_back(c);
+            Stream& st = streams[r.stream];
+            st.slots[r.slot].in_flight = false;
+            --st.pending;
+            --outstanding;
+        }
+    }
+    cv_done.notify_all();
+}
 
 // which: 0 the plain frames of the batch, 1 the learned ones, 2 all; the batch's request
 // list is cleared once its last frames are reported.
@@ -140,7 +194,7 @@ void yoro_server_ctx::complete(Batch& b, long long t_done, int which)
             c.submit_ns = r.submit_ns;
             c.launch_ns = b.launch_ns;
             c.done_ns = t_done;
-            c.batch_frames = (int)b.req.size();
+            c.batch_frames = b.frames;
             c.status = b.status;
             c.inpainted = b.status == YORO_OK ? r.inpainted : 0;
             done.push_back(c);
@@ -206,17 +260,44 @@ void yoro_server_ctx::run()
                 b.status = (yoro_status)yoro::synthesize_batch_zt((int)frames.size(), frames.data(),
                                                                   any_learned ? zts.data() : nullptr, cs);
                 b.any_learned = any_learned;
+                b.frames = (int)b.req.size();
                 if (b.status == YORO_OK && cudaEventRecord(b.synth, cs) != cudaSuccess) b.status = YORO_ECUDA;
-                // learned inpainting of those frames, one after another on the same stream
+                // learned inpainting of those frames, one after another on the inpainting
+                // stream, once the synthesis is done
+                cudaStream_t done_on = cs;
+                if (b.status == YORO_OK && any_learned && net) {
+                    if (cudaStreamWaitEvent(ci, b.synth, 0) != cudaSuccess) b.status = YORO_ECUDA;
+                    done_on = ci;
+                }
                 for (size_t i = 0; i < b.req.size(); ++i) {
                     b.req[i].inpainted = 0;
                     if (b.status != YORO_OK || !zts[i] || !net) continue;
                     const yoro_frame& f = frames[i];
                     b.req[i].inpainted =
-                        yoro_unet_inpaint(net, f.w, f.h, f.near_, f.out_color, f.out_hole_mask, zts[i], f.depth, cs) ==
+                        yoro_unet_inpaint(net, f.w, f.h, f.near_, f.out_color, f.out_hole_mask, zts[i], f.depth, ci) ==
                         YORO_OK;
                 }
-                if (b.status == YORO_OK && cudaEventRecord(b.done, cs) != cudaSuccess) b.status = YORO_ECUDA;
+                // The learned frames are reported by a host function after their inpainting, so
+                // that the batch retires (and the scheduler moves on) when the synthesis is done.
+                if (b.status == YORO_OK && done_on == ci) {
+                    LearnedDone* ld = new (std::nothrow) LearnedDone();
+                    if (ld) {
+                        ld->server = this;
+                        ld->launch_ns = b.launch_ns;
+                        ld->batch_frames = (int)b.req.size();
+                        std::vector<Request> plain;
+                        for (const Request& r : b.req) (r.learned ? ld->req : plain).push_back(r);
+                        if (cudaLaunchHostFunc(ci, learned_done, ld) == cudaSuccess) {
+                            b.req.swap(plain);
+                            b.any_learned = false;
+                            done_on = cs;
+                        } else {
+                            cudaGetLastError();
+                            delete ld;
+                        }
+                    }
+                }
+                if (b.status == YORO_OK && cudaEventRecord(b.done, done_on) != cudaSuccess) b.status = YORO_ECUDA;
                 ++count;
                 launched = true;
             }
@@ -334,8 +415,13 @@ yoro_server yoro_server_create(size_t memory_budget_bytes, int max_batch)
     }
     s->budget = memory_budget_bytes;
     s->max_batch = max_batch;
+    // The synthesis stream gets the highest scheduling priority and the inpainting stream
+    // the lowest: pending CTAs of a synthesis launch go to SMs ahead of the network's.
+    int prio_low = 0, prio_high = 0;
     bool ok = cudaGetDevice(&s->device) == cudaSuccess &&
-              cudaStreamCreateWithFlags(&s->cs, cudaStreamNonBlocking) == cudaSuccess;
+              cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high) == cudaSuccess &&
+              cudaStreamCreateWithPriority(&s->cs, cudaStreamNonBlocking, prio_high) == cudaSuccess &&
+              cudaStreamCreateWithPriority(&s->ci, cudaStreamNonBlocking, prio_low) == cudaSuccess;
     for (int i = 0; ok && i < kInFlight; ++i)
         ok = cudaEventCreateWithFlags(&s->ring[i].done, cudaEventBlockingSync | cudaEventDisableTiming) ==
                  cudaSuccess &&
@@ -348,6 +434,7 @@ yoro_server yoro_server_create(size_t memory_budget_bytes, int max_batch)
             if (b.synth) cudaEventDestroy(b.synth);
         }
         if (s->cs) cudaStreamDestroy(s->cs);
+        if (s->ci) cudaStreamDestroy(s->ci);
         delete s;
         yoro::set_last_create_error(YORO_ECUDA);
         return nullptr;
@@ -360,6 +447,7 @@ yoro_server yoro_server_create(size_t memory_budget_bytes, int max_batch)
             cudaEventDestroy(b.synth);
         }
         cudaStreamDestroy(s->cs);
+        cudaStreamDestroy(s->ci);
         delete s;
         yoro::set_last_create_error(YORO_ENOMEM);
         return nullptr;
@@ -382,6 +470,7 @@ void yoro_server_destroy(yoro_server s)
     if (s->fs) cudaStreamDestroy(s->fs);
     if (s->worker.joinable()) s->worker.join();
     cudaStreamSynchronize(s->cs);
+    cudaStreamSynchronize(s->ci);
     for (Stream& st : s->streams)
         if (st.block) cudaFree(st.block);
     for (Batch& b : s->ring) {
@@ -389,6 +478,7 @@ void yoro_server_destroy(yoro_server s)
         cudaEventDestroy(b.synth);
     }
     cudaStreamDestroy(s->cs);
+    cudaStreamDestroy(s->ci);
     delete s;
 }
 

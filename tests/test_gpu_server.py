@@ -304,8 +304,8 @@ def test_the_feeder_submits_from_device_sources(srv):
     assert sorted(r.tag for r in got) == list(range(100, 106)) and all(r.status == 0 for r in got)
     # the last frame sent (tag 105) was source 1; its slot holds that frame's result
     last = max(got, key=lambda r: r.tag)
-    fcfg, fc, fd = frames[1]
-    ref = oracle.synthesize(fc, fd, fcfg.fx, fcfg.fy, fcfg.cx, fcfg.cy, fcfg.ipd, fcfg.near, fcfg.far)
+    _, fc, fd = frames[1]  # synthesized with the stream's camera
+    ref = oracle.synthesize(fc, fd, cfg.fx, cfg.fy, cfg.cx, cfg.cy, cfg.ipd, cfg.near, cfg.far)
     assert np.array_equal(s.slot(a, last.slot)[2].cpu().numpy(), ref[0])
     # paced at 200 Hz: submissions at least ~5 ms apart
     s.feed(a, src, nframes=5, hz=200.0, tag0=200)
