@@ -2,9 +2,9 @@
 
 Run by ``test_gpu_debug_bounds.py`` as ``python tests/debug_bounds_check.py``: the
 process loads the debug-bounds library before any other call, synthesizes frames that
-exercise every kernel (fused single-frame launch with the default and variant kernels,
-the batch launch, the unfused launch, the intermediate-buffer and general-pose
-launches; tall bands,
+exercise every kernel (fused single-frame launch with the default and variant kernels
+and with the warped-depth output, the batch launch with and without it, the unfused
+launch, the intermediate-buffer and general-pose launches; tall bands,
 ragged widths, a wide-disparity camera), and checks for each that the status word stayed clear (no range check failed)
 and that the result still equals the CPU oracle byte for byte.  Then the self-test
 kernel must raise ``YORO_EDEVICE`` exactly once.  Prints ``debug-bounds OK`` at the end.
@@ -127,6 +127,42 @@ def main() -> None:
     assert st == 0, f"batch: status {yoro.STATUS.get(st, st)}"
     for i, fr in enumerate(frames):
         _same((fr["out_color"].cpu().numpy(), fr["out_mask"].cpu().numpy()), fr["ref"], f"batch frame {i}")
+
+    # the warped-depth instantiations: a single frame (yoro_synthesize_zt) and a batch
+    # with a learned stream in the serving loop (the batch kernel writing warped depth)
+    from paper_2506_15183_gb300 import server as srv
+
+    for (h, w, seed) in ((64, 333, 7), (1920, 1832, 8)):
+        c, d, cam = _ragged(h, w, seed)
+        hdl = yoro.yoro_create(**cam)
+        out = torch.empty((h, w, 4), dtype=torch.uint8, device=DEV)
+        mask = torch.empty((h, w), dtype=torch.uint8, device=DEV)
+        zt = torch.empty((h, w), dtype=torch.float32, device=DEV)
+        yoro.yoro_synthesize_zt(hdl, torch.from_numpy(c).to(DEV), torch.from_numpy(d).to(DEV), out, mask, zt)
+        st = yoro.yoro_stream_status(hdl)
+        assert st == 0, f"synthesize_zt {w}x{h}: status {yoro.STATUS.get(st, st)}"
+        _same((out.cpu().numpy(), mask.cpu().numpy()), _ref(c, d, cam), f"synthesize_zt {w}x{h}")
+        yoro.yoro_destroy(hdl)
+    c, d, cam = _ragged(71, 333, 11)
+    s = srv.Server(1 << 28, max_batch=4)
+    a = s.admit(**cam, slots=1, learned=True)
+    b = s.admit(**cam, slots=1)
+    for sid in (a, b):
+        ci, di, _, _ = s.slot(sid, 0)
+        ci.copy_(torch.from_numpy(c))
+        di.copy_(torch.from_numpy(d))
+    torch.cuda.synchronize()
+    s.submit(a, 0, tag=1)
+    s.submit(b, 0, tag=2)
+    s.drain()
+    assert all(r.status == 0 for r in s.poll())
+    st = yoro.yoro_stream_status(None)
+    assert st == 0, f"server batch with warped depth: status {yoro.STATUS.get(st, st)}"
+    ref = _ref(c, d, cam)
+    for sid in (a, b):
+        _, _, co, mo = s.slot(sid, 0)
+        _same((co.cpu().numpy(), mo.cpu().numpy()), ref, f"server stream {sid}")
+    s.close()
 
     yoro.yoro_debug_selftest()
     assert yoro.yoro_stream_status(None) == EDEVICE, "the self-test code was not reported"
