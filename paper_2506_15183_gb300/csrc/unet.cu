@@ -178,8 +178,9 @@ struct ConvArgs {
     int y_cstride, y_coff;
     int upsample;         // 1: pixel (yy, xx) goes to (2yy + a, 2xx + b), a, b in {0, 1}
     int relu;
-    int ncols;            // tensor-memory columns allocated (a power of two >= Cout, >= 32)
+    int ncols;            // tensor-memory columns allocated (a power of two >= mt Cout, >= 32)
     const int* count;     // optional: tiles at or after *count are skipped (the tile list's length)
+    int mt, stages;       // halo form: 128-pixel accumulators per CTA and copy stages
 };
 
 __global__ void __launch_bounds__(128, 1)
@@ -314,6 +315,178 @@ __global__ void __launch_bounds__(128, 1)
     }
 }
 
+// Halo form of the same convolution, for layers whose 128-pixel tile is whole rows of
+// one image: a CTA computes R = mt 128 / W whole rows of one image into mt accumulators
+// of 128 pixels (mt Cout tensor-memory columns).  A K step is one (channel block, dx)
+// pair rather than one (channel block, tap): a single activation box of R + 2 rows x W
+// pixels x 32 channels at column offset dx - 1 (rows y0 - 1 and y0 + R and columns -1 and
+// W lie outside the image and arrive as zeros) and the three weight boxes of the taps
+// (0, dx), (1, dx), (2, dx).  In NHWC the box is R + 2 rows of W pixels of 64 bytes, so
+// the operand of tap dy for accumulator j is the same box read from pixel row j 128 +
+// dy W: a start (j 128 + dy W) 64 bytes in, a whole number of 512-byte swizzle atoms
+// for W a multiple of 8, and the three dy taps share one copy.  Activation bytes copied
+// per output pixel: 3 (R + 2) / R boxes instead of 9; weight bytes: 1 / mt of the
+// one-tile form.
+constexpr int kMaxStages = 4;
+
+__global__ void __launch_bounds__(128, 1)
+    conv3x3_halo(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const ConvArgs a)
+{
+    extern __shared__ unsigned char smem_raw[];
+    const int mt = a.mt, S = a.stages;
+    const int tile_px = mt * kTileM;
+    const int hw = a.H * a.W;
+    if (a.count && (int)(((long long)blockIdx.x * tile_px) / hw) >= *a.count) return;  // no such tile (uniform)
+    unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                                           ~static_cast<uintptr_t>(1023));
+    const int R = tile_px / a.W;
+    const int a_bytes = (R + 2) * a.W * kKc * 2;
+    const int a_span = (a_bytes + 1023) & ~1023;
+    const int b_tap = a.Cout * kKc * 2;
+    const int stage_bytes = a_span + ((3 * b_tap + 1023) & ~1023);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + S * stage_bytes);
+    uint64_t* empty = full + kMaxStages;
+    uint64_t* done = empty + kMaxStages;
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
+    volatile int* counts = reinterpret_cast<volatile int*>(tslot + 1);  // [0] issued, [1] consumed
+    float* sbias = reinterpret_cast<float*>(smem + S * stage_bytes + 1024);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    const int cb_n = a.Cin / kKc;
+    const int nk = 3 * cb_n;  // K steps: (channel block, dx)
+    const int p0 = blockIdx.x * tile_px;
+    const int n0 = p0 / hw;
+    const int y0 = (p0 - n0 * hw) / a.W;
+    // K step k's copies into stage k % S: the activation box and the three weight boxes
+    auto issue = [&](int k) {
+        const int s = k % S;
+        const int cb = k / 3, dx = k - 3 * cb;
+        unsigned char* sa = smem + s * stage_bytes;
+        mbar_expect_tx(&full[s], (uint32_t)(a_bytes + 3 * b_tap));
+        tma_load_4d(sa, &tmA, &full[s], cb * kKc, dx - 1, y0 - 1, n0);
+#pragma unroll
+        for (int dy = 0; dy < 3; ++dy)
+            tma_load_2d(sa + a_span + dy * b_tap, &tmB, &full[s], (3 * dy + dx) * a.Cin + cb * kKc, 0);
+        counts[0] = k + 1;
+    };
+    const int first = nk < S ? nk : S;  // copies issued before the CTA-wide barrier
+
+    // The first copies start as soon as the barriers exist (their stages are free), while
+    // warp 1 allocates the tensor memory and the bias is staged in shared memory.
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(done, 1);
+        counts[0] = 0;
+        counts[1] = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        for (int k = 0; k < first; ++k) issue(k);
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                     "r"(a.ncols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    for (int c = threadIdx.x; c < a.Cout; c += blockDim.x) sbias[c] = __ldg(a.bias + c);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+    const uint64_t deadline = globaltimer() + kWaitNs;
+
+    if (warp == 0 && lane == 0) {  // copies
+        for (int k = first; k < nk; ++k) {
+            const int s = k % S;
+            if (!mbar_wait(&empty[s], ((k / S) & 1) ^ 1, deadline)) {
+                atomicOr(&g_unet_status, kUnetTimeout);
+                break;
+            }
+            issue(k);
+        }
+    } else if (warp == 1 && lane == 0) {  // MMAs
+        const uint32_t idesc = idesc_bf16(a.Cout);
+        for (int k = 0; k < nk; ++k) {
+            const int s = k % S;
+            if (!mbar_wait(&full[s], (k / S) & 1, deadline)) {
+                atomicOr(&g_unet_status, kUnetTimeout);
+                break;
+            }
+            tc_fence_after();
+            const uint32_t sa = smem_u32(smem + s * stage_bytes), sb = sa + a_span;
+            for (int dy = 0; dy < 3; ++dy) {
+                const uint32_t bt = sb + dy * b_tap;
+                for (int j = 0; j < mt; ++j) {
+                    const uint32_t at = sa + (uint32_t)(j * kTileM + dy * a.W) * (kKc * 2);
+                    const uint32_t d = tmem + (uint32_t)(j * a.Cout);
+                    mma_bf16(d, desc_sw64(at), desc_sw64(bt), idesc, (k > 0 || dy > 0) ? 1u : 0u);
+                    mma_bf16(d, desc_sw64(at + 32), desc_sw64(bt + 32), idesc, 1u);
+                }
+            }
+            mma_commit(&empty[s]);
+            counts[1] = k + 1;
+        }
+        mma_commit(done);  // arrives once every MMA issued above has completed
+    }
+    __syncwarp();
+
+    const bool ok = mbar_wait(done, 0, deadline + kWaitNs);
+    if (!ok) atomicOr(&g_unet_status, kUnetTimeout);
+    if (ok) {
+        tc_fence_after();
+        const int m = warp * 32 + lane;  // this thread's pixel of each 128-pixel tile = its TMEM lane
+        for (int j = 0; j < mt; ++j) {
+            const int p = p0 + j * kTileM + m;
+            const int n = p / hw, rem = p - n * hw, yy = rem / a.W, xx = rem - (rem / a.W) * a.W;
+            for (int c0 = 0; c0 < a.Cout; c0 += 32) {
+                uint32_t r[32];
+                tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(j * a.Cout + c0), r);
+                uint4 q[4];
+                uint32_t* qw = reinterpret_cast<uint32_t*>(q);
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    float v0 = __fadd_rn(__uint_as_float(r[2 * i]), sbias[c0 + 2 * i]);
+                    float v1 = __fadd_rn(__uint_as_float(r[2 * i + 1]), sbias[c0 + 2 * i + 1]);
+                    if (a.relu) {
+                        v0 = fmaxf(v0, 0.0f);
+                        v1 = fmaxf(v1, 0.0f);
+                    }
+                    qw[i] = pack_bf16x2(v0, v1);
+                }
+                if (!a.upsample) {
+                    uint4* dst = reinterpret_cast<uint4*>(a.y + ((size_t)p * a.y_cstride + a.y_coff + c0));
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) dst[i] = q[i];
+                } else {
+                    const int W2 = 2 * a.W, H2 = 2 * a.H;
+#pragma unroll
+                    for (int ab = 0; ab < 4; ++ab) {
+                        const size_t op = ((size_t)n * H2 + (2 * yy + (ab >> 1))) * W2 + (2 * xx + (ab & 1));
+                        uint4* dst = reinterpret_cast<uint4*>(a.y + (op * a.y_cstride + a.y_coff + c0));
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) dst[i] = q[i];
+                    }
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (threadIdx.x == 0) {  // copies still in flight after a timeout: wait for them (bounded)
+        const uint64_t d2 = globaltimer() + kWaitNs;
+        for (int k = counts[1]; k < counts[0]; ++k)
+            if (!mbar_wait(&full[k % S], (k / S) & 1, d2)) break;
+    }
+    __syncthreads();
+    if (warp == 1) {  // the allocating warp frees
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(a.ncols) : "memory");
+    }
+}
+
 // Driver entry point for tensor-map encoding, looked up once through the runtime (no
 // link against the driver library).
 using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -340,6 +513,41 @@ size_t conv_smem_bytes(int cout)
     const int b_bytes = cout * kKc * 2;
     const int stage = kABytes + ((b_bytes + 1023) & ~1023);
     return 1024 + (size_t)kStages * stage + (2 * kStages + 1) * 8 + 16;
+}
+
+// Halo form: bytes of one copy stage (activation box of R + 2 rows, three weight boxes).
+int halo_stage_bytes(int W, int rows, int cout)
+{
+    return ((((rows + 2) * W * kKc * 2) + 1023) & ~1023) + ((3 * cout * kKc * 2 + 1023) & ~1023);
+}
+
+// Halo form: the stages, then 1 KB of barriers and counters, then the bias (256 floats).
+size_t halo_smem_bytes(int stage_bytes, int stages)
+{
+    return 1024 + (size_t)stages * stage_bytes + 1024 + 256 * 4;
+}
+
+// Shared memory a halo-form CTA may take: at least two CTAs share an SM (228 KB, 1 KB
+// reserved per CTA); with two stages, three fit for Cout <= 64.
+constexpr int kHaloSmemBudget = 112 * 1024;
+
+// The halo form's shape for a layer, or mt = 0 where the one-tile form runs: whole-row
+// tiles of one image (W in 16..128), two accumulators of 128 pixels (R = 256 / W rows,
+// a divisor of H), Cout <= 128 (2 Cout tensor-memory columns), two copy stages within
+// the budget.  Two accumulators with two stages (three CTAs per SM for Cout <= 64, two
+// for Cout = 128) measured fastest on every layer of the network, against one or four
+// accumulators and two to four stages at one to four CTAs per SM: more CTAs per SM
+// overlap one CTA's set-up, last MMAs and epilogue with the others' copies.
+void halo_shape(int H, int W, int Cout, int* mt, int* stages)
+{
+    *mt = 0;
+    *stages = 0;
+    if (W < 16 || W > kTileM || kTileM % W || Cout > 128) return;
+    const int rows = 2 * kTileM / W;
+    if (rows > H || H % rows) return;
+    if (halo_smem_bytes(halo_stage_bytes(W, rows, Cout), 2) > (size_t)kHaloSmemBudget) return;
+    *mt = 2;
+    *stages = 2;
 }
 
 }  // namespace
@@ -414,6 +622,34 @@ cudaError_t unet_conv3x3(const void* x, int T, int H, int W, int Cin, const void
     a.relu = relu;
     a.ncols = Cout < 32 ? 32 : Cout;
     a.count = count;
+    a.mt = 0;
+    a.stages = kStages;
+    int mt = 0, stages = 0;
+    if (nb == 1) halo_shape(H, W, Cout, &mt, &stages);
+    if (mt) {
+        const int rows = mt * kTileM / W;
+        CUtensorMap th;
+        const cuuint32_t hbox[4] = {(cuuint32_t)kKc, (cuuint32_t)W, (cuuint32_t)(rows + 2), 1u};
+        if (enc(&th, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(x), adim, astr, hbox, one4,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+        a.mt = mt;
+        a.stages = stages;
+        int nc = 32;
+        while (nc < mt * Cout) nc *= 2;
+        a.ncols = nc;
+        static bool halo_configured = false;
+        if (!halo_configured) {
+            const cudaError_t e =
+                cudaFuncSetAttribute(conv3x3_halo, cudaFuncAttributeMaxDynamicSharedMemorySize, kHaloSmemBudget);
+            if (e != cudaSuccess) return e;
+            halo_configured = true;
+        }
+        const size_t hsmem = halo_smem_bytes(halo_stage_bytes(W, rows, Cout), stages);
+        conv3x3_halo<<<(unsigned)(pixels / (mt * kTileM)), 128, hsmem, stream>>>(th, tb, a);
+        return cudaGetLastError();
+    }
     const size_t smem = conv_smem_bytes(Cout);
     static bool configured = false;
     if (!configured) {

@@ -99,6 +99,15 @@ def test_conv_layer_matches_definition(un, T, H, W, cin, cout):
     _case(un, T, H, W, cin, cout, seed=100 + cin + cout)
 
 
+@pytest.mark.parametrize("T,H,W,cin,cout", [(1, 64, 128, 32, 32), (2, 8, 64, 64, 32), (1, 32, 16, 64, 128),
+                                              (1, 6, 64, 32, 32), (3, 16, 32, 32, 64)])
+def test_conv_row_bands(un, T, H, W, cin, cout):
+    """Both forms of the convolution: several row bands per image (whole-row halo boxes,
+    rows -1 and H outside the image read as zeros, W = 128 boxes), and heights that no band
+    of 256 pixels divides (the one-tile form)."""
+    _case(un, T, H, W, cin, cout, seed=200 + H + W + cin + cout)
+
+
 def test_conv_first_layer_padded_channels(un):
     """The 6 input channels padded to 32 with zero channels and zero weights."""
     _case(un, 1, 64, 64, 32, 32, seed=7, real_cin=6)
@@ -108,6 +117,8 @@ def test_conv_into_concat_buffer_and_upsampled(un):
     """Channel offset inside a wider buffer, and the 2x2 nearest-upsampling store."""
     _case(un, 2, 8, 8, 256, 256, seed=8, upsample=True, cy=384, coff=128)
     _case(un, 1, 32, 32, 64, 32, seed=9, cy=96, coff=0)
+    _case(un, 1, 32, 32, 64, 64, seed=11, upsample=True, cy=96, coff=32)
+    _case(un, 2, 16, 16, 128, 128, seed=12, upsample=True, cy=192, coff=64)
 
 
 def test_conv_without_relu(un):
