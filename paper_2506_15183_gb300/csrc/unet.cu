@@ -1,21 +1,28 @@
 // The learned hole inpainter on the tensor cores (sm_103a): a 4-level U-Net over
 // 64 x 64 tiles, BF16 weights and activations, FP32 accumulation.
 //
-// Each 3x3 convolution is an implicit GEMM: M = output pixels (128 per CTA tile, whole
-// rows of one or two tiles), N = output channels (32..256, one MMA tile), K = 9 taps x
-// input channels, taken 32 channels of one tap at a time.  A K step is two TMA tiled
-// loads into shared memory with 64-byte swizzle: the activation box {32 channels, W, Hb,
-// Nb} of NHWC bf16 at the tap's offset (the padding rows and columns are outside the
-// tensor and arrive as zeros), and the weight box {32, Cout} of the K-major weights
-// (k = tap * Cin + ci).  One thread issues the copies, another the tcgen05.mma (kind::f16,
-// BF16 operands, FP32 accumulator in tensor memory, two K = 16 steps per stage), with
-// mbarriers between them (4 stages).  The epilogue reads the accumulators with
-// tcgen05.ld, adds the bias, applies ReLU, rounds to BF16 and stores NHWC at a channel
-// offset of a wider buffer (so a decoder's concatenation is written in place), or, for
-// the layer below a decoder level, to the 2 x 2 pixels of the nearest upsampling.  One
-// CTA per 128-pixel tile: with 128 threads and 4 stages, several CTAs share an SM and
-// keep about 20 stages of copies in flight there (the narrow layers stream their
-// activations from L2 once per tap).
+// Each 3x3 convolution is an implicit GEMM: M = output pixels (128 per accumulator), N =
+// output channels (32..256, one MMA tile), K = taps x input channels, taken 32 channels
+// (64 bytes: the swizzle span) at a time.  Operands are TMA tiled loads into shared
+// memory with 64-byte swizzle (the zero padding of the convolution is the part of a box
+// outside the tensor, which TMA fills with zeros); one thread issues the copies, another
+// the tcgen05.mma (kind::f16, BF16 operands, FP32 accumulator in tensor memory, two
+// K = 16 steps per 32-channel slice), with mbarriers between them.  The epilogue reads
+// the accumulators with tcgen05.ld, adds the bias, applies ReLU, rounds to BF16 and
+// stores NHWC at a channel offset of a wider buffer (so a decoder's concatenation is
+// written in place), or, for the layer below a decoder level, to the 2 x 2 pixels of the
+// nearest upsampling.  Two forms:
+//   - conv3x3_halo, for tiles of whole rows of one image: a CTA computes 256 / W rows
+//     into two accumulators; a K step is one (channel block, dx) pair, a single box of
+//     the rows plus one above and below, shared by the three dy taps through the start
+//     address of the MMA operand (whole 512-byte swizzle atoms apart), and the three
+//     taps' weight boxes.  Each input pixel is copied 3 (R + 2) / R times instead of 9.
+//   - conv3x3_tc, one CTA per 128-pixel tile (the 8 x 8 level, where 128 pixels are two
+//     tiles, and 256 output channels): a K step is one (channel block, tap), the
+//     activation box {32 channels, W, rows, tiles} at the tap's offset and the weight box
+//     {32, Cout} of the K-major weights (k = tap * Cin + ci), in a 4-stage ring.
+// Both are one CTA of 128 threads per tile; several CTAs share an SM, so the copies of
+// one overlap the set-up, MMAs and epilogue of the others.
 //
 // Every wait on an mbarrier has a deadline (1 s of %globaltimer): a wait that runs out
 // records kUnetTimeout in a status word, the kernel waits (again bounded) for the copies
