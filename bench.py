@@ -644,7 +644,10 @@ def run_inpaint(args):
         "config": {"workload": f"{T} 64x64 tiles per step ({ntx * nty}: every tile of a 1832x1920 frame), 4-level "
                                "U-Net 32/64/128/256", "flops_per_tile": W.flops_per_tile(), "tiles": T},
         "roofline": {"bound": "tensor", "achieved": round(tflops, 2), "peak": peak, "unit": "TFLOP/s",
-                     "frac": round(tflops / peak, 4), "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst)"},
+                     "frac": round(tflops / peak, 4), "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst)",
+                     "traffic": None,
+                     "traffic_note": "the network is 14 convolution launches and small kernels; DRAM bytes per "
+                                     "convolution launch are in profiles/conv3x3_halo_inpaint_128tiles.md"},
         "frame_path_ms": {"p50": round(lat[len(lat) // 2], 3), "p99": round(lat[int(0.99 * (len(lat) - 1))], 3),
                           "what": "yoro_synthesize_zt + yoro_unet_inpaint on one 1832x1920 frame (hole tiles only)"},
     }), flush=True)
