@@ -116,6 +116,24 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, u
         : "memory");
 }
 
+// TMA tensor stores from shared memory (bulk-group completion): 4-D and 5-D boxes.
+__device__ __forceinline__ void tma_store_4d(const CUtensorMap* map, const void* src, int c0, int c1, int c2, int c3)
+{
+    asm volatile("cp.async.bulk.tensor.4d.global.shared::cta.bulk_group [%0, {%2, %3, %4, %5}], [%1];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(smem_u32(src)), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tma_store_5d(const CUtensorMap* map, const void* src, int c0, int c1, int c2, int c3,
+                                             int c4)
+{
+    asm volatile("cp.async.bulk.tensor.5d.global.shared::cta.bulk_group [%0, {%2, %3, %4, %5, %6}], [%1];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(smem_u32(src)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4)
+                 : "memory");
+}
+
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
@@ -190,8 +208,67 @@ struct ConvArgs {
     int mt, stages;       // halo form: 128-pixel accumulators per CTA and copy stages
 };
 
+// The epilogue of both forms: the CTA's mt accumulators of 128 pixels (pixel i of
+// accumulator j is the CTA tile's pixel 128 j + i, row-major over its rows) are read
+// back 32 channels at a time, the bias added, ReLU applied, rounded to BF16 and staged in
+// shared memory (`stg`, 1024-aligned: the copy stages, free once every MMA has
+// completed), one slice of 64 bytes per pixel for each 32 channels, in the 64-byte
+// swizzle (16-byte chunk k of pixel p at p 64 + (k ^ (p / 2 mod 4)) 16, so a warp's
+// writes meet no bank twice).  One thread then writes every slice with TMA tensor
+// stores: a box {32 channels, W, rows, images} at channel y_coff + 32 s, or, for the
+// nearest upsampling, the same box four times through a 5-D view of the output that
+// splits each coordinate into (pixel, replica).  The CTA ends once the stores have read
+// shared memory.
+__device__ __forceinline__ void epilogue_store(const ConvArgs& a, const CUtensorMap* tmY, uint32_t tmem,
+                                               unsigned char* stg, const float* bias, int mt, int n0, int y0)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m = warp * 32 + lane;  // this thread's pixel of each accumulator = its TMEM lane
+    const int slice = mt * kTileM * 64;
+    for (int c0 = 0; c0 < a.Cout; c0 += 32) {
+        unsigned char* sl = stg + (c0 >> 5) * slice;
+        for (int j = 0; j < mt; ++j) {
+            uint32_t r[32];
+            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(j * a.Cout + c0), r);
+            uint4 q[4];
+            uint32_t* qw = reinterpret_cast<uint32_t*>(q);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                float v0 = __fadd_rn(__uint_as_float(r[2 * i]), bias[c0 + 2 * i]);
+                float v1 = __fadd_rn(__uint_as_float(r[2 * i + 1]), bias[c0 + 2 * i + 1]);
+                if (a.relu) {
+                    v0 = fmaxf(v0, 0.0f);
+                    v1 = fmaxf(v1, 0.0f);
+                }
+                qw[i] = pack_bf16x2(v0, v1);
+            }
+            const int px = j * kTileM + m;
+            unsigned char* row = sl + px * 64;
+            const int sw = (px >> 1) & 3;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) *reinterpret_cast<uint4*>(row + ((k ^ sw) << 4)) = q[k];
+        }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // the writes, seen by the copy engine
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int c0 = 0; c0 < a.Cout; c0 += 32) {
+            const unsigned char* sl = stg + (c0 >> 5) * slice;
+            if (!a.upsample) {
+                tma_store_4d(tmY, sl, a.y_coff + c0, 0, y0, n0);
+            } else {
+#pragma unroll
+                for (int ab = 0; ab < 4; ++ab) tma_store_5d(tmY, sl, a.y_coff + c0, ab & 1, 0, ab >> 1, n0 * a.H + y0);
+            }
+        }
+        asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+        asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+    }
+}
+
 __global__ void __launch_bounds__(128, 1)
-    conv3x3_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const ConvArgs a)
+    conv3x3_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+               const __grid_constant__ CUtensorMap tmY, const ConvArgs a)
 {
     extern __shared__ unsigned char smem_raw[];
     if (a.count && (int)((blockIdx.x * kTileM) / (a.H * a.W)) >= *a.count) return;  // no such tile (uniform)
@@ -274,39 +351,7 @@ __global__ void __launch_bounds__(128, 1)
     if (!ok) atomicOr(&g_unet_status, kUnetTimeout);
     if (ok) {
         tc_fence_after();
-        const int m = warp * 32 + lane;  // this thread's pixel of the tile = its TMEM lane
-        const int p = p0 + m;
-        const int n = p / hw, rem = p - n * hw, yy = rem / a.W, xx = rem - (rem / a.W) * a.W;
-        for (int c0 = 0; c0 < a.Cout; c0 += 32) {
-            uint32_t r[32];
-            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
-            uint4 q[4];
-            uint32_t* qw = reinterpret_cast<uint32_t*>(q);
-#pragma unroll
-            for (int i = 0; i < 16; ++i) {
-                float v0 = __fadd_rn(__uint_as_float(r[2 * i]), __ldg(a.bias + c0 + 2 * i));
-                float v1 = __fadd_rn(__uint_as_float(r[2 * i + 1]), __ldg(a.bias + c0 + 2 * i + 1));
-                if (a.relu) {
-                    v0 = fmaxf(v0, 0.0f);
-                    v1 = fmaxf(v1, 0.0f);
-                }
-                qw[i] = pack_bf16x2(v0, v1);
-            }
-            if (!a.upsample) {
-                uint4* dst = reinterpret_cast<uint4*>(a.y + ((size_t)p * a.y_cstride + a.y_coff + c0));
-#pragma unroll
-                for (int i = 0; i < 4; ++i) dst[i] = q[i];
-            } else {
-                const int W2 = 2 * a.W, H2 = 2 * a.H;
-#pragma unroll
-                for (int ab = 0; ab < 4; ++ab) {
-                    const size_t op = ((size_t)n * H2 + (2 * yy + (ab >> 1))) * W2 + (2 * xx + (ab & 1));
-                    uint4* dst = reinterpret_cast<uint4*>(a.y + (op * a.y_cstride + a.y_coff + c0));
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) dst[i] = q[i];
-                }
-            }
-        }
+        epilogue_store(a, &tmY, tmem, smem, a.bias, 1, n0, y0);
     }
     tc_fence_before();
     __syncthreads();
@@ -337,7 +382,8 @@ __global__ void __launch_bounds__(128, 1)
 constexpr int kMaxStages = 4;
 
 __global__ void __launch_bounds__(128, 1)
-    conv3x3_halo(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const ConvArgs a)
+    conv3x3_halo(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                 const __grid_constant__ CUtensorMap tmY, const ConvArgs a)
 {
     extern __shared__ unsigned char smem_raw[];
     const int mt = a.mt, S = a.stages;
@@ -444,41 +490,7 @@ __global__ void __launch_bounds__(128, 1)
     if (!ok) atomicOr(&g_unet_status, kUnetTimeout);
     if (ok) {
         tc_fence_after();
-        const int m = warp * 32 + lane;  // this thread's pixel of each 128-pixel tile = its TMEM lane
-        for (int j = 0; j < mt; ++j) {
-            const int p = p0 + j * kTileM + m;
-            const int n = p / hw, rem = p - n * hw, yy = rem / a.W, xx = rem - (rem / a.W) * a.W;
-            for (int c0 = 0; c0 < a.Cout; c0 += 32) {
-                uint32_t r[32];
-                tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(j * a.Cout + c0), r);
-                uint4 q[4];
-                uint32_t* qw = reinterpret_cast<uint32_t*>(q);
-#pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    float v0 = __fadd_rn(__uint_as_float(r[2 * i]), sbias[c0 + 2 * i]);
-                    float v1 = __fadd_rn(__uint_as_float(r[2 * i + 1]), sbias[c0 + 2 * i + 1]);
-                    if (a.relu) {
-                        v0 = fmaxf(v0, 0.0f);
-                        v1 = fmaxf(v1, 0.0f);
-                    }
-                    qw[i] = pack_bf16x2(v0, v1);
-                }
-                if (!a.upsample) {
-                    uint4* dst = reinterpret_cast<uint4*>(a.y + ((size_t)p * a.y_cstride + a.y_coff + c0));
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) dst[i] = q[i];
-                } else {
-                    const int W2 = 2 * a.W, H2 = 2 * a.H;
-#pragma unroll
-                    for (int ab = 0; ab < 4; ++ab) {
-                        const size_t op = ((size_t)n * H2 + (2 * yy + (ab >> 1))) * W2 + (2 * xx + (ab & 1));
-                        uint4* dst = reinterpret_cast<uint4*>(a.y + (op * a.y_cstride + a.y_coff + c0));
-#pragma unroll
-                        for (int i = 0; i < 4; ++i) dst[i] = q[i];
-                    }
-                }
-            }
-        }
+        epilogue_store(a, &tmY, tmem, smem, sbias, mt, n0, y0);
     }
     tc_fence_before();
     __syncthreads();
@@ -553,6 +565,7 @@ void halo_shape(int H, int W, int Cout, int* mt, int* stages)
     const int rows = 2 * kTileM / W;
     if (rows > H || H % rows) return;
     if (halo_smem_bytes(halo_stage_bytes(W, rows, Cout), 2) > (size_t)kHaloSmemBudget) return;
+    if ((Cout / kKc) * 2 * kTileM * 64 > 2 * halo_stage_bytes(W, rows, Cout)) return;  // the epilogue's staging
     *mt = 2;
     *stages = 2;
 }
@@ -595,6 +608,7 @@ cudaError_t unet_conv3x3(const void* x, int T, int H, int W, int Cin, const void
     const long long pixels = (long long)T * H * W;
     if (pixels % kTileM || (nb > 1 && T % nb)) return cudaErrorInvalidValue;
     if (y_cstride % 8 || y_coff % 8 || y_coff + Cout > y_cstride) return cudaErrorInvalidValue;
+    if (reinterpret_cast<uintptr_t>(y) % 16) return cudaErrorInvalidValue;  // a TMA store's base
     EncodeTiled enc = encode_fn();
     if (!enc) return cudaErrorNotSupported;
 
@@ -614,6 +628,28 @@ cudaError_t unet_conv3x3(const void* x, int T, int H, int W, int Cin, const void
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return cudaErrorInvalidValue;
+
+    // The output map: the epilogue's box of 32 channels x the CTA's pixels (rows x W x
+    // images), or for the upsampling a 5-D view {channel, b, x, a, n H + y} of the 2H x 2W
+    // output with pixel (2y + a, 2x + b), whose box {32, 1, W, 1, rows} takes one replica.
+    const cuuint64_t cs = (cuuint64_t)y_cstride;
+    auto y_map = [&](CUtensorMap* m, int rows, int imgs) -> bool {
+        if (!upsample) {
+            const cuuint64_t d[4] = {cs, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)T};
+            const cuuint64_t st[3] = {cs * 2, (cuuint64_t)W * cs * 2, (cuuint64_t)H * W * cs * 2};
+            const cuuint32_t box[4] = {(cuuint32_t)kKc, (cuuint32_t)W, (cuuint32_t)rows, (cuuint32_t)imgs};
+            return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, y, d, st, box, one4, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                       CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+        }
+        const cuuint64_t d[5] = {cs, 2, (cuuint64_t)W, 2, (cuuint64_t)T * H};
+        const cuuint64_t st[4] = {cs * 2, 2 * cs * 2, (cuuint64_t)2 * W * cs * 2, (cuuint64_t)4 * W * cs * 2};
+        const cuuint32_t box[5] = {(cuuint32_t)kKc, 1, (cuuint32_t)W, 1, (cuuint32_t)(rows * imgs)};
+        const cuuint32_t one5[5] = {1, 1, 1, 1, 1};
+        return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, y, d, st, box, one5, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    };
 
     ConvArgs a;
     a.T = T;
@@ -641,6 +677,8 @@ cudaError_t unet_conv3x3(const void* x, int T, int H, int W, int Cin, const void
                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             return cudaErrorInvalidValue;
+        CUtensorMap ty;
+        if (!y_map(&ty, rows, 1)) return cudaErrorInvalidValue;
         a.mt = mt;
         a.stages = stages;
         int nc = 32;
@@ -654,7 +692,7 @@ cudaError_t unet_conv3x3(const void* x, int T, int H, int W, int Cin, const void
             halo_configured = true;
         }
         const size_t hsmem = halo_smem_bytes(halo_stage_bytes(W, rows, Cout), stages);
-        conv3x3_halo<<<(unsigned)(pixels / (mt * kTileM)), 128, hsmem, stream>>>(th, tb, a);
+        conv3x3_halo<<<(unsigned)(pixels / (mt * kTileM)), 128, hsmem, stream>>>(th, tb, ty, a);
         return cudaGetLastError();
     }
     const size_t smem = conv_smem_bytes(Cout);
@@ -665,7 +703,9 @@ cudaError_t unet_conv3x3(const void* x, int T, int H, int W, int Cin, const void
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    conv3x3_tc<<<(unsigned)(pixels / kTileM), 128, smem, stream>>>(ta, tb, a);
+    CUtensorMap ty;
+    if (!y_map(&ty, hb, nb)) return cudaErrorInvalidValue;
+    conv3x3_tc<<<(unsigned)(pixels / kTileM), 128, smem, stream>>>(ta, tb, ty, a);
     return cudaGetLastError();
 }
 
