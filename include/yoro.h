@@ -292,9 +292,9 @@ yoro_status yoro_debug_selftest(void* cuda_stream);
  * than yoro_noalloc_max_pixels() are rejected with YORO_ETOOBIG.  Every call looks up
  * that array's device address (cudaGetSymbolAddress, no allocation), so the address
  * stays right after a cudaDeviceReset(); the first call on a device also loads the
- * library's module there, so make that first call before any stream capture.  Every call clears the part of the
- * array it uses on cuda_stream, and every call on every stream shares the array, so
- * calls that could overlap on the GPU race: serialise them (one stream, or events).
+ * library's module there.  Every call clears the part of the array it uses on
+ * cuda_stream, and every call on every stream shares the array, so calls that could
+ * overlap on the GPU race: serialise them (one stream, or events).
  */
 yoro_status yoro_synthesize_noalloc(int w, int h, float fx, float fy, float cx, float cy, float ipd,
                                     float near_, float far_, const void* color_rgba8, const float* depth_f32,
