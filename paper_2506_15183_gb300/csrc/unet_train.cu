@@ -153,69 +153,91 @@ __global__ void relu_mask_kernel(const float* __restrict__ G, const uint16_t* __
     for (int i = threadIdx.x; i < C; i += blockDim.x) atomicAdd(&db[i], s[i]);
 }
 
-// dW[co][ci][tap] += sum over this block's pixels of dZ[p][co] * X[p shifted by the tap][ci]
-// (zero outside the tile).  32 x 32 (co, ci) tiles, 32 pixels per step through shared
-// memory; thread t takes co = t / 8 and four consecutive ci.
-__global__ void __launch_bounds__(256) dw_kernel(const uint16_t* __restrict__ dZ, const uint16_t* __restrict__ X,
-                                                 int xcs, int side, int cin, int cout, long long npx, int pix_per_block,
-                                                 float* __restrict__ dW)
+// The weight gradient with register tiles: dW[co][ci][tap] += sum over the block's pixels
+// of dZ[p][co] * X[p shifted by the tap][ci] (zero outside the tile).  A CTA takes a
+// CO_T x CI_T (co, ci) tile of one tap and a range of pixels, 32 pixels per step staged in
+// shared memory as floats (16-byte loads of 8 bfloat16 values; the tile side is a power
+// of two, so the shift is found with shifts and masks).  Thread (tc, ti) of group g keeps
+// the 4 x 4 products of co 4 tc .., ci 4 ti .. over the step's pixels g, g + G, ...
+// (G = 256 / (CO_T CI_T / 16) groups), each a fused multiply-add, and adds its sums to
+// dW at the end.  The channels a load covers lie inside X's channel stride (a layer whose
+// input channels are padded, the first, reads the zero padding); sums for ci >= cin are
+// dropped.
+template <int CO_T, int CI_T>
+__global__ void __launch_bounds__(256) dw_tiled_kernel(const uint16_t* __restrict__ dZ, const uint16_t* __restrict__ X,
+                                                      int xcs, int side_log2, int cin, int cout, long long npx,
+                                                      int pix_per_block, float* __restrict__ dW)
 {
-    __shared__ float sZ[32][33];
-    __shared__ __align__(16) float sX[32][36];
-    const int ci0 = blockIdx.x * 32, co0 = blockIdx.y * 32;
+    constexpr int TC = CO_T / 4, TI = CI_T / 4, G = 256 / (TC * TI);
+    __shared__ __align__(16) float sZ[32][CO_T + 4];
+    __shared__ __align__(16) float sX[32][CI_T + 4];
+    const int ci0 = blockIdx.x * CI_T, co0 = blockIdx.y * CO_T;
     const int tap = blockIdx.z % 9, split = blockIdx.z / 9;
     const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+    const int side = 1 << side_log2;
     const int t = threadIdx.x;
-    const int co_l = t >> 3, ci_l = (t & 7) * 4;
+    const int g = t / (TC * TI), r = t - g * (TC * TI);
+    const int tc = r / TI, ti = r - tc * TI;
     const long long p_begin = (long long)split * pix_per_block;
     const long long p_end = min(npx, p_begin + pix_per_block);
-    float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    float acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.0f;
     for (long long p0 = p_begin; p0 < p_end; p0 += 32) {
-        {  // load: row = t / 8 (pixel), 4 values at (t % 8) * 4
-            const int r = t >> 3, q = (t & 7) * 4;
-            const long long p = p0 + r;
-            float z[4] = {0.0f, 0.0f, 0.0f, 0.0f}, xv[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        // dZ rows of the step: 32 pixels x CO_T channels, 8 per load
+        for (int l = t; l < 32 * (CO_T / 8); l += 256) {
+            const int k = l / (CO_T / 8), c = (l - k * (CO_T / 8)) * 8;
+            const long long p = p0 + k;
+            uint4 u = make_uint4(0u, 0u, 0u, 0u);
+            if (p < p_end) u = *reinterpret_cast<const uint4*>(dZ + p * cout + co0 + c);
+            float4* dst = reinterpret_cast<float4*>(&sZ[k][c]);
+            dst[0] = make_float4(__uint_as_float(u.x << 16), __uint_as_float(u.x & 0xffff0000u),
+                                 __uint_as_float(u.y << 16), __uint_as_float(u.y & 0xffff0000u));
+            dst[1] = make_float4(__uint_as_float(u.z << 16), __uint_as_float(u.z & 0xffff0000u),
+                                 __uint_as_float(u.w << 16), __uint_as_float(u.w & 0xffff0000u));
+        }
+        // X at the tap's shift: 32 pixels x CI_T channels
+        for (int l = t; l < 32 * (CI_T / 8); l += 256) {
+            const int k = l / (CI_T / 8), c = (l - k * (CI_T / 8)) * 8;
+            const long long p = p0 + k;
+            uint4 u = make_uint4(0u, 0u, 0u, 0u);
             if (p < p_end) {
-                if (co0 + q < cout) {
-                    const uint2 u = *reinterpret_cast<const uint2*>(dZ + p * cout + co0 + q);
-                    z[0] = __uint_as_float(u.x << 16);
-                    z[1] = __uint_as_float(u.x & 0xffff0000u);
-                    z[2] = __uint_as_float(u.y << 16);
-                    z[3] = __uint_as_float(u.y & 0xffff0000u);
-                }
-                const long long x = p % side, rr = p / side, y = rr % side, tt = rr / side;
-                const long long ys = y + dy, xs = x + dx;
-                if (ys >= 0 && ys < side && xs >= 0 && xs < side && ci0 + q < cin) {
-                    const uint16_t* src = X + ((tt * side + ys) * side + xs) * xcs + ci0 + q;
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) xv[j] = (ci0 + q + j < cin) ? bf2f(src[j]) : 0.0f;
-                }
+                const int x = (int)(p & (side - 1)), y = (int)((p >> side_log2) & (side - 1));
+                const long long tt = p >> (2 * side_log2);
+                const int ys = y + dy, xs = x + dx;
+                if (ys >= 0 && ys < side && xs >= 0 && xs < side)
+                    u = *reinterpret_cast<const uint4*>(X + (((tt << side_log2) + ys) * side + xs) * xcs + ci0 + c);
             }
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                sZ[r][q + j] = z[j];
-                sX[r][q + j] = xv[j];
-            }
+            float4* dst = reinterpret_cast<float4*>(&sX[k][c]);
+            dst[0] = make_float4(__uint_as_float(u.x << 16), __uint_as_float(u.x & 0xffff0000u),
+                                 __uint_as_float(u.y << 16), __uint_as_float(u.y & 0xffff0000u));
+            dst[1] = make_float4(__uint_as_float(u.z << 16), __uint_as_float(u.z & 0xffff0000u),
+                                 __uint_as_float(u.w << 16), __uint_as_float(u.w & 0xffff0000u));
         }
         __syncthreads();
-#pragma unroll 8
-        for (int k = 0; k < 32; ++k) {
-            const float z = sZ[k][co_l];
-            const float4 xv = *reinterpret_cast<const float4*>(&sX[k][ci_l]);
-            acc[0] += z * xv.x;
-            acc[1] += z * xv.y;
-            acc[2] += z * xv.z;
-            acc[3] += z * xv.w;
+#pragma unroll 4
+        for (int k = g; k < 32; k += G) {
+            const float4 z = *reinterpret_cast<const float4*>(&sZ[k][4 * tc]);
+            const float4 x = *reinterpret_cast<const float4*>(&sX[k][4 * ti]);
+            const float zv[4] = {z.x, z.y, z.z, z.w}, xv[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = __fmaf_rn(zv[i], xv[j], acc[i][j]);
         }
         __syncthreads();
     }
-    const int co = co0 + co_l;
-    if (co < cout)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int co = co0 + 4 * tc + i;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            const int ci = ci0 + ci_l + j;
-            if (ci < cin) atomicAdd(&dW[((long long)co * cin + ci) * 9 + tap], acc[j]);
+            const int ci = ci0 + 4 * ti + j;
+            if (ci < cin) atomicAdd(&dW[((long long)co * cin + ci) * 9 + tap], acc[i][j]);
         }
+    }
 }
 
 // G[p][c] += DX[p * dcs + dcoff + c]
@@ -470,12 +492,24 @@ cudaError_t trainer_step(Trainer* t, const void* x, const uint8_t* gt, const uin
         relu_mask_kernel<<<blocks_for(nz), 256, 0, s>>>(t->G[i], io[i].y, io[i].ycs, io[i].ycoff, io[i].yup, side,
                                                         L.cout, nz, t->dZ, t->grads + t->boff[i]);
         {
-            const int tiles = (L.cin + 31) / 32 * (L.cout / 32) * 9;
-            long long ppb = 2048;
-            while (ppb > 256 && tiles * ((P + ppb - 1) / ppb) < 2048) ppb /= 2;
-            const dim3 grid((L.cin + 31) / 32, L.cout / 32, (unsigned)(9 * ((P + ppb - 1) / ppb)));
-            dw_kernel<<<grid, 256, 0, s>>>(t->dZ, io[i].x, io[i].xcs, side, L.cin, L.cout, P, (int)ppb,
-                                            t->grads + t->woff[i]);
+            // (co, ci) tiles of 64 where the channels allow, else 32; pixel ranges (multiples
+            // of 32) short enough for at least ~1,000 CTAs
+            const int cot = L.cout % 64 == 0 ? 64 : 32, cit = L.cin % 64 == 0 ? 64 : 32;
+            const int tiles = (L.cin + cit - 1) / cit * (L.cout / cot) * 9;
+            long long ppb = 4096;
+            while (ppb > 256 && tiles * ((P + ppb - 1) / ppb) < 1024) ppb /= 2;
+            const dim3 grid((L.cin + cit - 1) / cit, L.cout / cot, (unsigned)(9 * ((P + ppb - 1) / ppb)));
+            int ls = 0;
+            while ((1 << ls) < side) ++ls;
+            float* dw = t->grads + t->woff[i];
+            if (cot == 64 && cit == 64)
+                dw_tiled_kernel<64, 64><<<grid, 256, 0, s>>>(t->dZ, io[i].x, io[i].xcs, ls, L.cin, L.cout, P, (int)ppb, dw);
+            else if (cot == 64)
+                dw_tiled_kernel<64, 32><<<grid, 256, 0, s>>>(t->dZ, io[i].x, io[i].xcs, ls, L.cin, L.cout, P, (int)ppb, dw);
+            else if (cit == 64)
+                dw_tiled_kernel<32, 64><<<grid, 256, 0, s>>>(t->dZ, io[i].x, io[i].xcs, ls, L.cin, L.cout, P, (int)ppb, dw);
+            else
+                dw_tiled_kernel<32, 32><<<grid, 256, 0, s>>>(t->dZ, io[i].x, io[i].xcs, ls, L.cin, L.cout, P, (int)ppb, dw);
         }
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if (i == 0) break;
