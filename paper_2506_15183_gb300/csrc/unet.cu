@@ -12,8 +12,9 @@
 // stores NHWC at a channel offset of a wider buffer (so a decoder's concatenation is
 // written in place), or, for the layer below a decoder level, to the 2 x 2 pixels of the
 // nearest upsampling.  Two forms:
-//   - conv3x3_halo, for tiles of whole rows of one image: a CTA computes 256 / W rows
-//     into two accumulators; a K step is one (channel block, dx) pair, a single box of
+//   - conv3x3_halo, for tiles of whole rows of one image: a band of 256 / W rows goes
+//     into two accumulators (each CTA walks bands blockIdx.x, + gridDim.x, ..., as many
+//     CTAs as fit on the SMs at once); a K step is one (channel block, dx) pair, a single box of
 //     the rows plus one above and below, shared by the three dy taps through the start
 //     address of the MMA operand (whole 512-byte swizzle atoms apart), and the three
 //     taps' weight boxes.  Each input pixel is copied 3 (R + 2) / R times instead of 9.
@@ -21,8 +22,8 @@
 //     tiles, and 256 output channels): a K step is one (channel block, tap), the
 //     activation box {32 channels, W, rows, tiles} at the tap's offset and the weight box
 //     {32, Cout} of the K-major weights (k = tap * Cin + ci), in a 4-stage ring.
-// Both are one CTA of 128 threads per tile; several CTAs share an SM, so the copies of
-// one overlap the set-up, MMAs and epilogue of the others.
+// Both use CTAs of 128 threads, several per SM, so the copies of one overlap the set-up,
+// MMAs and epilogue of the others.
 //
 // Every wait on an mbarrier has a deadline (1 s of %globaltimer): a wait that runs out
 // records kUnetTimeout in a status word, the kernel waits (again bounded) for the copies
@@ -383,16 +384,18 @@ constexpr int kMaxStages = 4;
 
 __global__ void __launch_bounds__(128, 1)
     conv3x3_halo(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                 const __grid_constant__ CUtensorMap tmY, const ConvArgs a)
+                 const __grid_constant__ CUtensorMap tmY, const ConvArgs a, int nbands)
 {
     extern __shared__ unsigned char smem_raw[];
     const int mt = a.mt, S = a.stages;
     const int tile_px = mt * kTileM;
-    const int hw = a.H * a.W;
-    if (a.count && (int)(((long long)blockIdx.x * tile_px) / hw) >= *a.count) return;  // no such tile (uniform)
+    const int R = tile_px / a.W;
+    const int bands_per_tile = a.H / R;
+    // bands of tiles at or after *count are skipped (the tile list's length)
+    const int live = a.count ? min(nbands, *a.count * bands_per_tile) : nbands;
+    if ((int)blockIdx.x >= live) return;  // uniform
     unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                                            ~static_cast<uintptr_t>(1023));
-    const int R = tile_px / a.W;
     const int a_bytes = (R + 2) * a.W * kKc * 2;
     const int a_span = (a_bytes + 1023) & ~1023;
     const int b_tap = a.Cout * kKc * 2;
@@ -401,18 +404,16 @@ __global__ void __launch_bounds__(128, 1)
     uint64_t* empty = full + kMaxStages;
     uint64_t* done = empty + kMaxStages;
     uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
-    volatile int* counts = reinterpret_cast<volatile int*>(tslot + 1);  // [0] issued, [1] consumed
+    volatile int* counts = reinterpret_cast<volatile int*>(tslot + 1);  // [0] issued, [1] consumed, [2] abort
     float* sbias = reinterpret_cast<float*>(smem + S * stage_bytes + 1024);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     const int cb_n = a.Cin / kKc;
-    const int nk = 3 * cb_n;  // K steps: (channel block, dx)
-    const int p0 = blockIdx.x * tile_px;
-    const int n0 = p0 / hw;
-    const int y0 = (p0 - n0 * hw) / a.W;
-    // K step k's copies into stage k % S: the activation box and the three weight boxes
-    auto issue = [&](int k) {
-        const int s = k % S;
+    const int nk = 3 * cb_n;  // K steps of a band: (channel block, dx)
+    // K step kk of the CTA (band kk / nk of its walk, step kk % nk) into stage kk % S
+    auto issue = [&](int kk, int n0, int y0) {
+        const int s = kk % S;
+        const int k = kk % nk;
         const int cb = k / 3, dx = k - 3 * cb;
         unsigned char* sa = smem + s * stage_bytes;
         mbar_expect_tx(&full[s], (uint32_t)(a_bytes + 3 * b_tap));
@@ -420,7 +421,7 @@ __global__ void __launch_bounds__(128, 1)
 #pragma unroll
         for (int dy = 0; dy < 3; ++dy)
             tma_load_2d(sa + a_span + dy * b_tap, &tmB, &full[s], (3 * dy + dx) * a.Cin + cb * kKc, 0);
-        counts[0] = k + 1;
+        counts[0] = kk + 1;
     };
     const int first = nk < S ? nk : S;  // copies issued before the CTA-wide barrier
 
@@ -434,9 +435,11 @@ __global__ void __launch_bounds__(128, 1)
         mbar_init(done, 1);
         counts[0] = 0;
         counts[1] = 0;
+        counts[2] = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        for (int k = 0; k < first; ++k) issue(k);
+        const int b0 = blockIdx.x, n0 = b0 / bands_per_tile, y0 = (b0 - n0 * bands_per_tile) * R;
+        for (int k = 0; k < first; ++k) issue(k, n0, y0);
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
@@ -449,52 +452,69 @@ __global__ void __launch_bounds__(128, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tslot;
-    const uint64_t deadline = globaltimer() + kWaitNs;
 
-    if (warp == 0 && lane == 0) {  // copies
-        for (int k = first; k < nk; ++k) {
-            const int s = k % S;
-            if (!mbar_wait(&empty[s], ((k / S) & 1) ^ 1, deadline)) {
-                atomicOr(&g_unet_status, kUnetTimeout);
-                break;
-            }
-            issue(k);
-        }
-    } else if (warp == 1 && lane == 0) {  // MMAs
-        const uint32_t idesc = idesc_bf16(a.Cout);
-        for (int k = 0; k < nk; ++k) {
-            const int s = k % S;
-            if (!mbar_wait(&full[s], (k / S) & 1, deadline)) {
-                atomicOr(&g_unet_status, kUnetTimeout);
-                break;
-            }
-            tc_fence_after();
-            const uint32_t sa = smem_u32(smem + s * stage_bytes), sb = sa + a_span;
-            for (int dy = 0; dy < 3; ++dy) {
-                const uint32_t bt = sb + dy * b_tap;
-                for (int j = 0; j < mt; ++j) {
-                    const uint32_t at = sa + (uint32_t)(j * kTileM + dy * a.W) * (kKc * 2);
-                    const uint32_t d = tmem + (uint32_t)(j * a.Cout);
-                    mma_bf16(d, desc_sw64(at), desc_sw64(bt), idesc, (k > 0 || dy > 0) ? 1u : 0u);
-                    mma_bf16(d, desc_sw64(at + 32), desc_sw64(bt + 32), idesc, 1u);
+    // The CTA walks bands blockIdx.x, + gridDim.x, ...: per band its K steps, then the
+    // epilogue; the barriers' phases run on across bands (step kk of the walk), and the
+    // accumulators are reused once every thread's reads of them are done.
+    int it = 0;
+    for (int band = blockIdx.x; band < live; band += gridDim.x, ++it) {
+        const int n0 = band / bands_per_tile, y0 = (band - n0 * bands_per_tile) * R;
+        const uint64_t deadline = globaltimer() + kWaitNs;
+        if (warp == 0 && lane == 0) {  // copies
+            for (int k = it == 0 ? first : 0; k < nk; ++k) {
+                const int kk = it * nk + k, s = kk % S;
+                if (!mbar_wait(&empty[s], ((kk / S) & 1) ^ 1, deadline)) {
+                    atomicOr(&g_unet_status, kUnetTimeout);
+                    counts[2] = 1;
+                    break;
                 }
+                issue(kk, n0, y0);
             }
-            mma_commit(&empty[s]);
-            counts[1] = k + 1;
+        } else if (warp == 1 && lane == 0) {  // MMAs
+            const uint32_t idesc = idesc_bf16(a.Cout);
+            for (int k = 0; k < nk; ++k) {
+                const int kk = it * nk + k, s = kk % S;
+                if (!mbar_wait(&full[s], (kk / S) & 1, deadline)) {
+                    atomicOr(&g_unet_status, kUnetTimeout);
+                    counts[2] = 1;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t sa = smem_u32(smem + s * stage_bytes), sb = sa + a_span;
+                for (int dy = 0; dy < 3; ++dy) {
+                    const uint32_t bt = sb + dy * b_tap;
+                    for (int j = 0; j < mt; ++j) {
+                        const uint32_t at = sa + (uint32_t)(j * kTileM + dy * a.W) * (kKc * 2);
+                        const uint32_t d = tmem + (uint32_t)(j * a.Cout);
+                        mma_bf16(d, desc_sw64(at), desc_sw64(bt), idesc, (k > 0 || dy > 0) ? 1u : 0u);
+                        mma_bf16(d, desc_sw64(at + 32), desc_sw64(bt + 32), idesc, 1u);
+                    }
+                }
+                mma_commit(&empty[s]);
+                counts[1] = kk + 1;
+            }
+            mma_commit(done);  // arrives once every MMA issued above has completed
         }
-        mma_commit(done);  // arrives once every MMA issued above has completed
-    }
-    __syncwarp();
-
-    const bool ok = mbar_wait(done, 0, deadline + kWaitNs);
-    if (!ok) atomicOr(&g_unet_status, kUnetTimeout);
-    if (ok) {
+        __syncwarp();
+        const bool ok = mbar_wait(done, it & 1, deadline + kWaitNs);
+        if (!ok) {
+            atomicOr(&g_unet_status, kUnetTimeout);
+            counts[2] = 1;
+        }
+        __syncthreads();
+        const bool go = ok && !counts[2];  // the same for every thread (read after the barrier)
+        if (go) {
+            tc_fence_after();
+            epilogue_store(a, &tmY, tmem, smem, sbias, mt, n0, y0);
+        }
+        // every thread's reads of the accumulators are done before the next band's MMAs
+        tc_fence_before();
+        __syncthreads();
         tc_fence_after();
-        epilogue_store(a, &tmY, tmem, smem, sbias, mt, n0, y0);
+        if (!go) break;
     }
-    tc_fence_before();
     __syncthreads();
-    if (threadIdx.x == 0) {  // copies still in flight after a timeout: wait for them (bounded)
+    if (threadIdx.x == 0 && counts[2]) {  // copies still in flight after a timeout: wait for them (bounded)
         const uint64_t d2 = globaltimer() + kWaitNs;
         for (int k = counts[1]; k < counts[0]; ++k)
             if (!mbar_wait(&full[k % S], (k / S) & 1, d2)) break;
@@ -587,6 +607,24 @@ unsigned unet_status_take()
 // channels, Cin a multiple of 32) with K-major weights wk (Cout rows of 9 Cin, k = (3 dy +
 // dx) Cin + ci) and bias, ReLU if relu, into y at channel offset y_coff of a tensor with
 // y_cstride channels (upsample: into the 2H x 2W grid of the nearest upsampling).
+// Shared memory of one SM (228 KB) and the SM count of the current device.
+constexpr size_t kSmemPerSm = 228 * 1024;
+
+int sm_count()
+{
+    static int n = 0;
+    if (!n) {
+        int dev = 0, v = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) !=
+                                                      cudaSuccess || v < 1) {
+            cudaGetLastError();
+            return 148;
+        }
+        n = v;
+    }
+    return n;
+}
+
 // Needs T H W a multiple of 128, W in {8, 16, 32, 64, 128} with 128 / W rows per tile or
 // whole tiles per 128 pixels, Cout in {32, 64, 128, 256}.  Returns cudaErrorInvalidValue
 // for shapes it does not take.
@@ -692,7 +730,11 @@ cudaError_t unet_conv3x3(const void* x, int T, int H, int W, int Cin, const void
             halo_configured = true;
         }
         const size_t hsmem = halo_smem_bytes(halo_stage_bytes(W, rows, Cout), stages);
-        conv3x3_halo<<<(unsigned)(pixels / (mt * kTileM)), 128, hsmem, stream>>>(th, tb, ty, a);
+        // as many CTAs as fit at once (shared memory; registers allow 5), each walking bands
+        const int nbands = (int)(pixels / (mt * kTileM));
+        const int per_sm = std::min(5, (int)(kSmemPerSm / (hsmem + 1024)));
+        const int grid = std::min(nbands, std::max(per_sm, 1) * sm_count());
+        conv3x3_halo<<<(unsigned)grid, 128, hsmem, stream>>>(th, tb, ty, a, nbands);
         return cudaGetLastError();
     }
     const size_t smem = conv_smem_bytes(Cout);
