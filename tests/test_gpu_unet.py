@@ -284,3 +284,63 @@ def test_inpaint_frame(un, w, h):
     assert np.all(got[hole][:, 3] == 255)
     net.close()
     syn.close()
+
+
+def test_inpaint_frame_without_holes(un):
+    """IPD 0: every pixel is reached, the hole-cell list is empty, every convolution
+    launch finds no band to compute, and the frame comes back byte for byte."""
+    import paper_2506_15183_gb300 as yoro
+    from paper_2506_15183_gb300 import scene
+
+    cfg = scene.small_config().replace(w=200, h=136, ipd=0.0)
+    c, d, _ = scene.render(cfg, 4)
+    syn = yoro.Synthesizer(**cfg.camera())
+    rgba = torch.empty((cfg.h, cfg.w, 4), dtype=torch.uint8, device="cuda")
+    mask = torch.empty((cfg.h, cfg.w), dtype=torch.uint8, device="cuda")
+    zt = torch.empty((cfg.h, cfg.w), dtype=torch.float32, device="cuda")
+    dg = torch.from_numpy(d).cuda()
+    yoro.yoro_synthesize_zt(syn.handle, torch.from_numpy(c).cuda(), dg, rgba, mask, zt)
+    torch.cuda.synchronize()
+    assert int(mask.sum()) == 0
+    before = rgba.clone()
+    net = _net(un, _weights(13), max_w=cfg.w, max_h=cfg.h)
+    net.inpaint(rgba, mask, zt, dg, cfg.near)
+    assert un.status() == 0
+    assert torch.equal(rgba, before)
+    net.close()
+    syn.close()
+
+
+def test_inpaint_reused_network_matches_a_fresh_one(un):
+    """A network that just repainted another frame (a different scene, more hole cells)
+    repaints the next one to the same bytes as a network that never ran: nothing of the
+    earlier call's tiles or barrier phases carries over."""
+    import paper_2506_15183_gb300 as yoro
+
+    p = _weights(17)
+    results = []
+    for first in (None, 7):
+        net = _net(un, p, max_w=256, max_h=256)
+        if first is not None:
+            cfg0, c0, d0, _ = _frame_tiles(first)
+            syn0 = yoro.Synthesizer(**cfg0.camera())
+            r0 = torch.empty((256, 256, 4), dtype=torch.uint8, device="cuda")
+            m0 = torch.empty((256, 256), dtype=torch.uint8, device="cuda")
+            z0 = torch.empty((256, 256), dtype=torch.float32, device="cuda")
+            d0g = torch.from_numpy(d0).cuda()
+            yoro.yoro_synthesize_zt(syn0.handle, torch.from_numpy(c0).cuda(), d0g, r0, m0, z0)
+            net.inpaint(r0, m0, z0, d0g, cfg0.near)
+            syn0.close()
+        cfg, c, d, _ = _frame_tiles(2)
+        syn = yoro.Synthesizer(**cfg.camera())
+        rgba = torch.empty((256, 256, 4), dtype=torch.uint8, device="cuda")
+        mask = torch.empty((256, 256), dtype=torch.uint8, device="cuda")
+        zt = torch.empty((256, 256), dtype=torch.float32, device="cuda")
+        dg = torch.from_numpy(d).cuda()
+        yoro.yoro_synthesize_zt(syn.handle, torch.from_numpy(c).cuda(), dg, rgba, mask, zt)
+        net.inpaint(rgba, mask, zt, dg, cfg.near)
+        assert un.status() == 0
+        results.append(rgba.cpu().numpy())
+        net.close()
+        syn.close()
+    assert np.array_equal(results[0], results[1])
