@@ -93,6 +93,28 @@ yoro_status yoro_unet_forward(yoro_unet u, const void* x, int T, float* rgb, voi
 yoro_status yoro_unet_inpaint(yoro_unet u, int w, int h, float near_, void* rgba, const unsigned char* mask,
                               const float* zt, const float* src_depth, void* cuda_stream);
 
+/* One frame of yoro_unet_inpaint_batch(): the arguments of yoro_unet_inpaint(). */
+typedef struct {
+    int w, h;
+    float near_;
+    void* rgba;
+    const unsigned char* mask;
+    const float* zt;
+    const float* src_depth;
+} yoro_unet_frame;
+
+/*
+ * yoro_unet_inpaint() of n frames (each as described there, sizes up to the handle's
+ * maximum) in as few passes of the network as its buffers allow: the frames' hole cells
+ * form one list, so a pass fills the tensor cores with the cells of several frames.  Each
+ * frame's result is the same bytes as yoro_unet_inpaint() of that frame alone (the
+ * network treats every cell on its own).  Frames are grouped in order, up to 32 and up to
+ * the handle's tile capacity (max(max_tiles, cells of a max_w x max_h frame)) per pass.
+ * Every frame is checked before any work is enqueued: the first failing frame's status is
+ * returned and nothing runs.  The frames must not overlap one another.
+ */
+yoro_status yoro_unet_inpaint_batch(yoro_unet u, int n, const yoro_unet_frame* frames, void* cuda_stream);
+
 /*
  * The network inputs of a frame's hole tiles, as yoro_unet_inpaint() builds them (the
  * windows of the hole cells, shifted inward at the last column and row): x_out receives

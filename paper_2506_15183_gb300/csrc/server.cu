@@ -262,20 +262,33 @@ void yoro_server_ctx::run()
                 b.any_learned = any_learned;
                 b.frames = (int)b.req.size();
                 if (b.status == YORO_OK && cudaEventRecord(b.synth, cs) != cudaSuccess) b.status = YORO_ECUDA;
-                // learned inpainting of those frames, one after another on the inpainting
-                // stream, once the synthesis is done
+                // learned inpainting of those frames on the inpainting stream, once the
+                // synthesis is done
                 cudaStream_t done_on = cs;
                 if (b.status == YORO_OK && any_learned && net) {
                     if (cudaStreamWaitEvent(ci, b.synth, 0) != cudaSuccess) b.status = YORO_ECUDA;
                     done_on = ci;
                 }
+                // all of them in one call: their hole cells share the network's passes
+                std::vector<yoro_unet_frame> lf;
+                std::vector<size_t> li;
                 for (size_t i = 0; i < b.req.size(); ++i) {
                     b.req[i].inpainted = 0;
                     if (b.status != YORO_OK || !zts[i] || !net) continue;
                     const yoro_frame& f = frames[i];
-                    b.req[i].inpainted =
-                        yoro_unet_inpaint(net, f.w, f.h, f.near_, f.out_color, f.out_hole_mask, zts[i], f.depth, ci) ==
-                        YORO_OK;
+                    lf.push_back(yoro_unet_frame{f.w, f.h, f.near_, f.out_color, f.out_hole_mask, zts[i], f.depth});
+                    li.push_back(i);
+                }
+                if (!lf.empty()) {
+                    if (yoro_unet_inpaint_batch(net, (int)lf.size(), lf.data(), ci) == YORO_OK) {
+                        for (size_t i : li) b.req[i].inpainted = 1;
+                    } else {  // a frame the inpainter does not take: the others one by one
+                        for (size_t k = 0; k < lf.size(); ++k) {
+                            const yoro_unet_frame& u = lf[k];
+                            b.req[li[k]].inpainted = yoro_unet_inpaint(net, u.w, u.h, u.near_, u.rgba, u.mask, u.zt,
+                                                                       u.src_depth, ci) == YORO_OK;
+                        }
+                    }
                 }
                 // The learned frames are reported by a host function after their inpainting, so
                 // that the batch retires (and the scheduler moves on) when the synthesis is done.

@@ -760,17 +760,50 @@ constexpr int kWidths[kLevels] = {32, 64, 128, 256};
 
 // ---- small CUDA-core kernels around the convolutions
 
-// Per 64 x 64 tile of a w x h frame: 1 if it holds a hole pixel (mask == 1).
-__global__ void tile_flags_kernel(const uint8_t* __restrict__ mask, int w, int h, int ntx, int* __restrict__ flags)
+// The frames of one inpainting launch.  Their cell grids are concatenated: cell c of frame
+// f (c = ty * ntx + tx) is entry off[f] + c, so their hole cells form one list and one pass
+// of the network takes them all.
+constexpr int kMaxInpaintFrames = 32;
+
+struct FrameTable {
+    int n;
+    int off[kMaxInpaintFrames + 1];  // off[n]: cells of all frames
+    int w[kMaxInpaintFrames], h[kMaxInpaintFrames], ntx[kMaxInpaintFrames];
+    float near_[kMaxInpaintFrames];
+    uint32_t* rgba[kMaxInpaintFrames];
+    const uint8_t* mask[kMaxInpaintFrames];
+    const float* zt[kMaxInpaintFrames];
+    const float* zsrc[kMaxInpaintFrames];
+};
+
+// Frame of concatenated cell g.
+__device__ __forceinline__ int table_frame(const FrameTable& ft, int g)
 {
-    const int tx = blockIdx.x, ty = blockIdx.y;
+    int lo = 0, hi = ft.n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (ft.off[mid] <= g) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Per 64 x 64 cell of each frame (blockIdx.x: cell, blockIdx.y: frame): 1 if it holds a
+// hole pixel (mask == 1), at the cell's entry of the concatenated grids.
+__global__ void tile_flags_kernel(const __grid_constant__ FrameTable ft, int* __restrict__ flags)
+{
+    const int f = blockIdx.y, cell = blockIdx.x;
+    const int w = ft.w[f], h = ft.h[f], ntx = ft.ntx[f];
+    if (cell >= ntx * ((h + kTile - 1) / kTile)) return;  // uniform
+    const int tx = cell % ntx, ty = cell / ntx;
+    const uint8_t* mask = ft.mask[f];
     int any = 0;
     for (int i = threadIdx.x; i < kTile * kTile; i += blockDim.x) {
         const int x = tx * kTile + (i & (kTile - 1)), y = ty * kTile + (i >> 6);
         if (x < w && y < h && mask[(size_t)y * w + x]) any = 1;
     }
     any = __syncthreads_or(any);
-    if (threadIdx.x == 0) flags[ty * ntx + tx] = any;
+    if (threadIdx.x == 0) flags[ft.off[f] + cell] = any;
 }
 
 // Ordered list of the flagged tiles (index ty * ntx + tx) and its length, one CTA.
@@ -829,28 +862,30 @@ __device__ __forceinline__ int window_origin(int t, int size) { return max(0, mi
 // at holes; the hole mask; near / warped depth, 0 at holes; near / source depth), rounded
 // to bfloat16, then 26 zero channels.
 // Pixels outside the frame (frames smaller than a tile) are all zero.
-__global__ void tile_input_kernel(const uint32_t* __restrict__ rgba, const uint8_t* __restrict__ mask,
-                                  const float* __restrict__ zt, const float* __restrict__ zsrc, int w, int h,
-                                  int ntx, float near_, const int* __restrict__ list, const int* __restrict__ count,
-                                  uint16_t* __restrict__ x)
+__global__ void tile_input_kernel(const __grid_constant__ FrameTable ft, const int* __restrict__ list,
+                                  const int* __restrict__ count, uint16_t* __restrict__ x)
 {
     const int ti = blockIdx.y;
     if (ti >= *count) return;
     const int p = blockIdx.x * blockDim.x + threadIdx.x;  // pixel of the tile
     if (p >= kTile * kTile) return;
-    const int tile = list[ti];
+    const int g = list[ti];
+    const int f = table_frame(ft, g);
+    const int tile = g - ft.off[f];
+    const int w = ft.w[f], h = ft.h[f], ntx = ft.ntx[f];
+    const float near_ = ft.near_[f];
     const int gx = window_origin(tile % ntx, w) + (p & (kTile - 1)), gy = window_origin(tile / ntx, h) + (p >> 6);
     float c[kInCh] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
     if (gx < w && gy < h) {
         const size_t o = (size_t)gy * w + gx;
-        const bool hole = mask[o] != 0;
-        const uint32_t v = rgba[o];
+        const bool hole = ft.mask[f][o] != 0;
+        const uint32_t v = ft.rgba[f][o];
         c[0] = __fdiv_rn((float)(v & 255u), 255.0f);
         c[1] = __fdiv_rn((float)((v >> 8) & 255u), 255.0f);
         c[2] = __fdiv_rn((float)((v >> 16) & 255u), 255.0f);
-        if (!hole) c[4] = __fdiv_rn(near_, fmaxf(zt[o], near_));
+        if (!hole) c[4] = __fdiv_rn(near_, fmaxf(ft.zt[f][o], near_));
         c[3] = hole ? 1.0f : 0.0f;
-        c[5] = __fdiv_rn(near_, fmaxf(zsrc[o], near_));
+        c[5] = __fdiv_rn(near_, fmaxf(ft.zsrc[f][o], near_));
     }
     uint4 q[4] = {};
     uint32_t* qw = reinterpret_cast<uint32_t*>(q);
@@ -899,27 +934,11 @@ __global__ void maxpool_kernel(const uint16_t* __restrict__ x, int T, int H, int
     }
 }
 
-// The output layer: a 1x1 convolution of the 32 channels (FP32 sums in channel order,
-// then the bias) and the logistic sigmoid 1 / (1 + exp(-z)).  mode 0: the three colors of
-// every pixel of every tile to rgb (T x 64 x 64 x 3 floats).  mode 1: compose into a frame:
-// each hole pixel of a listed tile's cell takes rint(clamp(c, 0, 1) * 255) per color and
-// alpha 255 (the pixels of the window outside the cell belong to the neighbouring tile).
-__global__ void output_kernel(const uint16_t* __restrict__ a, const float* __restrict__ wo,
-                              const float* __restrict__ bo, int T, const int* __restrict__ count, int mode,
-                              float* __restrict__ rgb, const int* __restrict__ list, int ntx, int w, int h,
-                              const uint8_t* __restrict__ mask, uint32_t* __restrict__ frame)
+// The output layer at pixel p of tile ti: a 1x1 convolution of the 32 channels (FP32 sums
+// in channel order, then the bias) and the logistic sigmoid 1 / (1 + exp(-z)).
+__device__ __forceinline__ void net_colors(const uint16_t* __restrict__ a, const float* __restrict__ wo,
+                                           const float* __restrict__ bo, int ti, int p, float (&col)[3])
 {
-    const int ti = blockIdx.y;
-    if (ti >= T || (count && ti >= *count)) return;
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= kTile * kTile) return;
-    int gx = 0, gy = 0;
-    if (mode == 1) {
-        const int tile = list[ti], tx = tile % ntx, ty = tile / ntx;
-        gx = window_origin(tx, w) + (p & (kTile - 1));
-        gy = window_origin(ty, h) + (p >> 6);
-        if (gx < kTile * tx || gy < kTile * ty || gx >= w || gy >= h || !mask[(size_t)gy * w + gx]) return;
-    }
     const uint4* src = reinterpret_cast<const uint4*>(a + ((size_t)ti * kTile * kTile + p) * 32);
     float v[32];
 #pragma unroll
@@ -932,7 +951,6 @@ __global__ void output_kernel(const uint16_t* __restrict__ a, const float* __res
             v[8 * i + 2 * k + 1] = __uint_as_float(qw[k] & 0xffff0000u);
         }
     }
-    float col[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         float acc = 0.0f;
@@ -941,18 +959,49 @@ __global__ void output_kernel(const uint16_t* __restrict__ a, const float* __res
         const float z = __fadd_rn(acc, bo[c]);
         col[c] = __fdiv_rn(1.0f, __fadd_rn(1.0f, expf(-z)));
     }
-    if (mode == 0) {
-        float* o = rgb + ((size_t)ti * kTile * kTile + p) * 3;
-        o[0] = col[0];
-        o[1] = col[1];
-        o[2] = col[2];
-    } else {
-        uint32_t out = 0xff000000u;
+}
+
+// The three colors of every pixel of the first T tiles to rgb (T x 64 x 64 x 3 floats).
+__global__ void output_kernel(const uint16_t* __restrict__ a, const float* __restrict__ wo,
+                              const float* __restrict__ bo, int T, float* __restrict__ rgb)
+{
+    const int ti = blockIdx.y;
+    if (ti >= T) return;
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= kTile * kTile) return;
+    float col[3];
+    net_colors(a, wo, bo, ti, p, col);
+    float* o = rgb + ((size_t)ti * kTile * kTile + p) * 3;
+    o[0] = col[0];
+    o[1] = col[1];
+    o[2] = col[2];
+}
+
+// Compose into the frames: each hole pixel of a listed tile's cell takes rint(clamp(c, 0,
+// 1) * 255) per color and alpha 255 (the pixels of the window outside the cell belong to
+// the neighbouring tile).
+__global__ void compose_kernel(const uint16_t* __restrict__ a, const float* __restrict__ wo,
+                               const float* __restrict__ bo, const int* __restrict__ count,
+                               const int* __restrict__ list, const __grid_constant__ FrameTable ft)
+{
+    const int ti = blockIdx.y;
+    if (ti >= *count) return;
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= kTile * kTile) return;
+    const int g = list[ti];
+    const int f = table_frame(ft, g);
+    const int tile = g - ft.off[f];
+    const int w = ft.w[f], h = ft.h[f], ntx = ft.ntx[f];
+    const int tx = tile % ntx, ty = tile / ntx;
+    const int gx = window_origin(tx, w) + (p & (kTile - 1)), gy = window_origin(ty, h) + (p >> 6);
+    if (gx < kTile * tx || gy < kTile * ty || gx >= w || gy >= h || !ft.mask[f][(size_t)gy * w + gx]) return;
+    float col[3];
+    net_colors(a, wo, bo, ti, p, col);
+    uint32_t out = 0xff000000u;
 #pragma unroll
-        for (int c = 0; c < 3; ++c)
-            out |= (uint32_t)rintf(__fmul_rn(fminf(fmaxf(col[c], 0.0f), 1.0f), 255.0f)) << (8 * c);
-        frame[(size_t)gy * w + gx] = out;
-    }
+    for (int c = 0; c < 3; ++c)
+        out |= (uint32_t)rintf(__fmul_rn(fminf(fmaxf(col[c], 0.0f), 1.0f), 255.0f)) << (8 * c);
+    ft.rgba[f][(size_t)gy * w + gx] = out;
 }
 
 void host_bf16_impl(const float* src, size_t n, uint16_t* dst)
@@ -975,8 +1024,7 @@ void host_bf16(const float* src, size_t n, uint16_t* dst) { host_bf16_impl(src, 
 
 cudaError_t unet_output_rgb(const UnetNet* n, int T, float* rgb, cudaStream_t s)
 {
-    output_kernel<<<dim3(16, (unsigned)T), 256, 0, s>>>(n->d0b, n->wout, n->wout + 96, T, nullptr, 0, rgb, nullptr, 0,
-                                                      0, 0, nullptr, nullptr);
+    output_kernel<<<dim3(16, (unsigned)T), 256, 0, s>>>(n->d0b, n->wout, n->wout + 96, T, rgb);
     return cudaGetLastError();
 }
 
@@ -1170,7 +1218,7 @@ yoro_unet yoro_unet_create(const float* params, long long n_params, int max_tile
     }
     c->max_w = max_w;
     c->max_h = max_h;
-    c->net = yoro::unet_create(params, (size_t)n_params, tiles, std::max(grid_tiles, 1));
+    c->net = yoro::unet_create(params, (size_t)n_params, tiles, tiles);  // flags and list hold `tiles` cells
     if (!c->net) {
         delete c;
         return nullptr;
@@ -1194,55 +1242,127 @@ yoro_status yoro_unet_forward(yoro_unet u, const void* x, int T, float* rgb, voi
     if (cudaMemcpyAsync(u->net->in0, x, (size_t)T * 64 * 64 * 32 * 2, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
         return YORO_ECUDA;
     if (yoro::unet_run(u->net, T, nullptr, s) != cudaSuccess) return YORO_ECUDA;
-    yoro::output_kernel<<<dim3(16, (unsigned)T), 256, 0, s>>>(u->net->d0b, u->net->wout, u->net->wout + 96, T,
-                                                            nullptr, 0, rgb, nullptr, 0, 0, 0, nullptr, nullptr);
+    yoro::output_kernel<<<dim3(16, (unsigned)T), 256, 0, s>>>(u->net->d0b, u->net->wout, u->net->wout + 96, T, rgb);
     return cudaGetLastError() == cudaSuccess ? YORO_OK : YORO_ECUDA;
 }
 
-yoro_status yoro_unet_inpaint(yoro_unet u, int w, int h, float near_, void* rgba, const unsigned char* mask,
-                              const float* zt, const float* src_depth, void* cuda_stream)
+}  // extern "C"
+
+namespace {
+
+// Checks of one frame of the inpainting entry points; YORO_OK, or the status to return.
+yoro_status check_frame(const yoro_unet_ctx* u, int w, int h, float near_, const void* rgba,
+                        const unsigned char* mask, const float* zt, const float* src_depth)
 {
-    if (!u || w < 0 || h < 0 || !(near_ > 0.0f) || !std::isfinite(near_)) return YORO_EINVAL;
+    if (w < 0 || h < 0 || !(near_ > 0.0f) || !std::isfinite(near_)) return YORO_EINVAL;
     if ((size_t)w * h == 0) return YORO_OK;
     if (w > u->max_w || h > u->max_h) return YORO_ETOOBIG;
     if (!rgba || !mask || !zt || !src_depth) return YORO_EINVAL;
     if (((uintptr_t)rgba | (uintptr_t)zt | (uintptr_t)src_depth) & 3u) return YORO_EALIGN;
+    return YORO_OK;
+}
+
+// Appends frame i to the table (its cells after those already there).
+void table_add(yoro::FrameTable& ft, const yoro_unet_frame& fr)
+{
+    const int k = ft.n;
+    ft.w[k] = fr.w;
+    ft.h[k] = fr.h;
+    ft.ntx[k] = (fr.w + 63) / 64;
+    ft.near_[k] = fr.near_;
+    ft.rgba[k] = static_cast<uint32_t*>(fr.rgba);
+    ft.mask[k] = fr.mask;
+    ft.zt[k] = fr.zt;
+    ft.zsrc[k] = fr.src_depth;
+    ft.off[k + 1] = ft.off[k] + ft.ntx[k] * ((fr.h + 63) / 64);
+    ft.n = k + 1;
+}
+
+// One pass of the network over the hole cells of the table's frames: the cells' flags, the
+// list of the flagged ones and its length on the device (launches cover every cell; those
+// past the list's length return at once), the inputs, the 14 layers, the composition.
+yoro_status inpaint_table(yoro_unet_ctx* u, const yoro::FrameTable& ft, cudaStream_t s)
+{
     yoro::UnetNet* n = u->net;
-    const cudaStream_t s = (cudaStream_t)cuda_stream;
-    const int ntx = (w + 63) / 64, nty = (h + 63) / 64;
-    yoro::tile_flags_kernel<<<dim3(ntx, nty), 256, 0, s>>>(mask, w, h, ntx, n->flags);
-    yoro::tile_list_kernel<<<1, 1024, 0, s>>>(n->flags, ntx * nty, n->list, n->count);
-    const int T = ntx * nty;  // launches cover every tile; those past the list's length return at once
-    yoro::tile_input_kernel<<<dim3(16, (unsigned)T), 256, 0, s>>>(static_cast<const uint32_t*>(rgba), mask, zt,
-                                                                src_depth, w, h, ntx, near_, n->list, n->count,
-                                                                n->in0);
+    const int total = ft.off[ft.n];
+    int maxcells = 0;
+    for (int f = 0; f < ft.n; ++f) maxcells = std::max(maxcells, ft.off[f + 1] - ft.off[f]);
+    if (total == 0) return YORO_OK;
+    yoro::tile_flags_kernel<<<dim3((unsigned)maxcells, (unsigned)ft.n), 256, 0, s>>>(ft, n->flags);
+    yoro::tile_list_kernel<<<1, 1024, 0, s>>>(n->flags, total, n->list, n->count);
+    yoro::tile_input_kernel<<<dim3(16, (unsigned)total), 256, 0, s>>>(ft, n->list, n->count, n->in0);
     if (cudaGetLastError() != cudaSuccess) return YORO_ECUDA;
-    if (yoro::unet_run(n, T, n->count, s) != cudaSuccess) return YORO_ECUDA;
-    yoro::output_kernel<<<dim3(16, (unsigned)T), 256, 0, s>>>(n->d0b, n->wout, n->wout + 96, T, n->count, 1,
-                                                            nullptr, n->list, ntx, w, h, mask,
-                                                            static_cast<uint32_t*>(rgba));
+    if (yoro::unet_run(n, total, n->count, s) != cudaSuccess) return YORO_ECUDA;
+    yoro::compose_kernel<<<dim3(16, (unsigned)total), 256, 0, s>>>(n->d0b, n->wout, n->wout + 96, n->count, n->list,
+                                                                 ft);
     return cudaGetLastError() == cudaSuccess ? YORO_OK : YORO_ECUDA;
+}
+
+}  // namespace
+
+extern "C" {
+
+yoro_status yoro_unet_inpaint(yoro_unet u, int w, int h, float near_, void* rgba, const unsigned char* mask,
+                              const float* zt, const float* src_depth, void* cuda_stream)
+{
+    if (!u) return YORO_EINVAL;
+    const yoro_status st = check_frame(u, w, h, near_, rgba, mask, zt, src_depth);
+    if (st != YORO_OK || (size_t)w * h == 0) return st;
+    yoro::FrameTable ft;
+    ft.n = 0;
+    ft.off[0] = 0;
+    table_add(ft, yoro_unet_frame{w, h, near_, rgba, mask, zt, src_depth});
+    return inpaint_table(u, ft, (cudaStream_t)cuda_stream);
+}
+
+yoro_status yoro_unet_inpaint_batch(yoro_unet u, int n, const yoro_unet_frame* frames, void* cuda_stream)
+{
+    if (!u || n < 0 || (n > 0 && !frames)) return YORO_EINVAL;
+    for (int i = 0; i < n; ++i) {
+        const yoro_unet_frame& fr = frames[i];
+        const yoro_status st = check_frame(u, fr.w, fr.h, fr.near_, fr.rgba, fr.mask, fr.zt, fr.src_depth);
+        if (st != YORO_OK) return st;
+    }
+    // groups of frames whose cells fit the network's buffers, up to kMaxInpaintFrames each
+    const int capacity = std::min(u->net->max_tiles, u->net->max_grid_tiles);
+    yoro::FrameTable ft;
+    ft.n = 0;
+    ft.off[0] = 0;
+    for (int i = 0; i < n; ++i) {
+        const yoro_unet_frame& fr = frames[i];
+        if ((size_t)fr.w * fr.h == 0) continue;
+        const int cells = ((fr.w + 63) / 64) * ((fr.h + 63) / 64);
+        if (ft.n == yoro::kMaxInpaintFrames || (ft.n > 0 && ft.off[ft.n] + cells > capacity)) {
+            const yoro_status st = inpaint_table(u, ft, (cudaStream_t)cuda_stream);
+            if (st != YORO_OK) return st;
+            ft.n = 0;
+        }
+        table_add(ft, fr);
+    }
+    return ft.n ? inpaint_table(u, ft, (cudaStream_t)cuda_stream) : YORO_OK;
 }
 
 yoro_status yoro_unet_prepare(yoro_unet u, int w, int h, float near_, const void* rgba, const unsigned char* mask,
                               const float* zt, const float* src_depth, void* x_out, int max_out, int* list_host,
                               int* count_host, void* cuda_stream)
 {
-    if (!u || w < 0 || h < 0 || !(near_ > 0.0f) || !std::isfinite(near_) || !list_host || !count_host)
-        return YORO_EINVAL;
+    if (!u || !list_host || !count_host) return YORO_EINVAL;
     *count_host = 0;
-    if ((size_t)w * h == 0) return YORO_OK;
-    if (w > u->max_w || h > u->max_h) return YORO_ETOOBIG;
+    yoro_status st = check_frame(u, w, h, near_, rgba, mask, zt, src_depth);
+    if (st != YORO_OK || (size_t)w * h == 0) return st;
     const int ntx = (w + 63) / 64, nty = (h + 63) / 64;
-    if (!rgba || !mask || !zt || !src_depth || !x_out || max_out < ntx * nty) return YORO_EINVAL;
-    if (((uintptr_t)rgba | (uintptr_t)zt | (uintptr_t)src_depth) & 3u || ((uintptr_t)x_out & 15u)) return YORO_EALIGN;
+    if (!x_out || max_out < ntx * nty) return YORO_EINVAL;
+    if ((uintptr_t)x_out & 15u) return YORO_EALIGN;
     yoro::UnetNet* n = u->net;
     const cudaStream_t s = (cudaStream_t)cuda_stream;
-    yoro::tile_flags_kernel<<<dim3(ntx, nty), 256, 0, s>>>(mask, w, h, ntx, n->flags);
+    yoro::FrameTable ft;
+    ft.n = 0;
+    ft.off[0] = 0;
+    table_add(ft, yoro_unet_frame{w, h, near_, const_cast<void*>(rgba), mask, zt, src_depth});
+    yoro::tile_flags_kernel<<<dim3((unsigned)(ntx * nty), 1), 256, 0, s>>>(ft, n->flags);
     yoro::tile_list_kernel<<<1, 1024, 0, s>>>(n->flags, ntx * nty, n->list, n->count);
-    yoro::tile_input_kernel<<<dim3(16, (unsigned)(ntx * nty)), 256, 0, s>>>(
-        static_cast<const uint32_t*>(rgba), mask, zt, src_depth, w, h, ntx, near_, n->list, n->count,
-        static_cast<uint16_t*>(x_out));
+    yoro::tile_input_kernel<<<dim3(16, (unsigned)(ntx * nty)), 256, 0, s>>>(ft, n->list, n->count,
+                                                                          static_cast<uint16_t*>(x_out));
     if (cudaGetLastError() != cudaSuccess) return YORO_ECUDA;
     if (cudaMemcpyAsync(count_host, n->count, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaMemcpyAsync(list_host, n->list, (size_t)ntx * nty * 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||

@@ -72,6 +72,21 @@ def status(stream=None) -> int:
     return _lib().yoro_unet_status(_stream(stream))
 
 
+class UnetFrame(ctypes.Structure):
+    """yoro_unet_frame: one frame of yoro_unet_inpaint_batch."""
+    _fields_ = [("w", ctypes.c_int), ("h", ctypes.c_int), ("near_", ctypes.c_float), ("rgba", ctypes.c_void_p),
+                ("mask", ctypes.c_void_p), ("zt", ctypes.c_void_p), ("src_depth", ctypes.c_void_p)]
+
+
+def _check_frame_tensors(rgba, mask, zt, src_depth):
+    h, w = mask.shape
+    for t, dt, shp, name in ((rgba, torch.uint8, (h, w, 4), "rgba"), (mask, torch.uint8, (h, w), "mask"),
+                             (zt, torch.float32, (h, w), "zt"), (src_depth, torch.float32, (h, w), "src_depth")):
+        if not t.is_cuda or t.dtype != dt or tuple(t.shape) != shp or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous CUDA {dt} tensor {shp}")
+    return w, h
+
+
 def _lib_net():
     lib = _lib()
     if not hasattr(lib, "_net_declared"):
@@ -88,6 +103,8 @@ def _lib_net():
         lib.yoro_unet_inpaint.restype = I
         lib.yoro_unet_prepare.argtypes = [P, I, I, F, P, P, P, P, P, I, P, P, P]
         lib.yoro_unet_prepare.restype = I
+        lib.yoro_unet_inpaint_batch.argtypes = [P, I, ctypes.POINTER(UnetFrame), P]
+        lib.yoro_unet_inpaint_batch.restype = I
         lib._net_declared = True
     return lib
 
@@ -128,14 +145,21 @@ class Inpainter:
     def inpaint(self, rgba: torch.Tensor, mask: torch.Tensor, zt: torch.Tensor, src_depth: torch.Tensor,
                 near: float, stream=None) -> None:
         """In place: hole pixels of rgba (h, w, 4) uint8 take the network's colors."""
-        h, w = mask.shape
-        for t, dt, shp, name in ((rgba, torch.uint8, (h, w, 4), "rgba"), (mask, torch.uint8, (h, w), "mask"),
-                                 (zt, torch.float32, (h, w), "zt"), (src_depth, torch.float32, (h, w), "src_depth")):
-            if not t.is_cuda or t.dtype != dt or tuple(t.shape) != shp or not t.is_contiguous():
-                raise ValueError(f"{name} must be a contiguous CUDA {dt} tensor {shp}")
+        w, h = _check_frame_tensors(rgba, mask, zt, src_depth)
         _check(_lib_net().yoro_unet_inpaint(self.ptr, w, h, float(near), rgba.data_ptr(), mask.data_ptr(),
                                             zt.data_ptr(), src_depth.data_ptr(), _stream(stream)),
                "yoro_unet_inpaint")
+
+    def inpaint_batch(self, frames, stream=None) -> None:
+        """yoro_unet_inpaint_batch: frames = [(rgba, mask, zt, src_depth, near), ...], each
+        repainted in place as inpaint() would, in as few passes of the network as fit."""
+        arr = (UnetFrame * max(1, len(frames)))()
+        for i, (rgba, mask, zt, src_depth, near) in enumerate(frames):
+            w, h = _check_frame_tensors(rgba, mask, zt, src_depth)
+            arr[i] = UnetFrame(w, h, float(near), rgba.data_ptr(), mask.data_ptr(), zt.data_ptr(),
+                               src_depth.data_ptr())
+        _check(_lib_net().yoro_unet_inpaint_batch(self.ptr, len(frames), arr, _stream(stream)),
+               "yoro_unet_inpaint_batch")
 
     def prepare(self, rgba, mask, zt, src_depth, near: float, x_out: torch.Tensor, stream=None) -> np.ndarray:
         """The network inputs of the frame's hole tiles into x_out[:count]; returns the tile

@@ -344,3 +344,66 @@ def test_inpaint_reused_network_matches_a_fresh_one(un):
         net.close()
         syn.close()
     assert np.array_equal(results[0], results[1])
+
+
+def test_inpaint_batch_matches_single_frames(un):
+    """yoro_unet_inpaint_batch: frames of three sizes and scenes in one call (and, with a
+    network whose buffers hold fewer cells than the batch, in several passes) give each
+    frame the bytes yoro_unet_inpaint gives it alone."""
+    import paper_2506_15183_gb300 as yoro
+
+    p = _weights(19)
+    specs = [(5, 256, 256), (6, 200, 136), (7, 256, 192)]
+    inputs = []
+    for seed, w, h in specs:
+        cfg, c, d, _ = _frame_tiles(seed, w, h)
+        syn = yoro.Synthesizer(**cfg.camera())
+        rgba = torch.empty((h, w, 4), dtype=torch.uint8, device="cuda")
+        mask = torch.empty((h, w), dtype=torch.uint8, device="cuda")
+        zt = torch.empty((h, w), dtype=torch.float32, device="cuda")
+        dg = torch.from_numpy(d).cuda()
+        yoro.yoro_synthesize_zt(syn.handle, torch.from_numpy(c).cuda(), dg, rgba, mask, zt)
+        syn.close()
+        inputs.append((rgba, mask, zt, dg, cfg.near))
+    torch.cuda.synchronize()
+    single = []
+    net = _net(un, p, max_w=256, max_h=256)
+    for rgba, mask, zt, dg, near in inputs:
+        r = rgba.clone()
+        net.inpaint(r, mask, zt, dg, near)
+        single.append(r)
+    for max_tiles in (0, 20):  # 0: one pass (capacity 16 cells x 3 frames fits 48); 20: several
+        net2 = _net(un, p, max_tiles=max_tiles or 48, max_w=256, max_h=256)
+        outs = [(rgba.clone(), mask, zt, dg, near) for rgba, mask, zt, dg, near in inputs]
+        net2.inpaint_batch(outs)
+        assert un.status() == 0
+        for (r, *_), ref_r in zip(outs, single):
+            assert torch.equal(r, ref_r)
+        net2.close()
+    net.close()
+
+
+def test_inpaint_batch_rejects_before_running(un):
+    """A frame larger than the network takes makes the whole call fail with
+    YORO_ETOOBIG, and no frame of it is touched."""
+    import paper_2506_15183_gb300 as yoro
+
+    cfg, c, d, _ = _frame_tiles(5, 256, 256)
+    syn = yoro.Synthesizer(**cfg.camera())
+    rgba = torch.empty((256, 256, 4), dtype=torch.uint8, device="cuda")
+    mask = torch.empty((256, 256), dtype=torch.uint8, device="cuda")
+    zt = torch.empty((256, 256), dtype=torch.float32, device="cuda")
+    dg = torch.from_numpy(d).cuda()
+    yoro.yoro_synthesize_zt(syn.handle, torch.from_numpy(c).cuda(), dg, rgba, mask, zt)
+    torch.cuda.synchronize()
+    before = rgba.clone()
+    net = _net(un, _weights(3), max_w=128, max_h=128)
+    small = torch.zeros((64, 64, 4), dtype=torch.uint8, device="cuda")
+    with pytest.raises(yoro.YoroError):
+        net.inpaint_batch([(small, torch.ones((64, 64), dtype=torch.uint8, device="cuda"),
+                            torch.zeros((64, 64), device="cuda"), torch.ones((64, 64), device="cuda"), 0.05),
+                           (rgba, mask, zt, dg, cfg.near)])
+    torch.cuda.synchronize()
+    assert torch.equal(rgba, before) and int(small.sum()) == 0
+    net.close()
+    syn.close()
