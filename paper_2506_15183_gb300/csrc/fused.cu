@@ -713,16 +713,18 @@ __global__ void __launch_bounds__(NT, MINB) fused_batch(const __grid_constant__ 
 
 // P3 alone over an image that is already resolved in global memory: the reached pixels'
 // colors in f.out, their depths in zt, the hole mask in f.mask (the row-downsampled
-// intermediate buffer's full-resolution image).  Each band's window is loaded (the
-// reached bitmasks by ballot over the mask bytes, depths and colors of the reached
-// pixels), then filled exactly as the fused kernel fills its bands.
-template <int NT>
+// intermediate buffer's and the general pose's full-resolution image).  Each band's window
+// is loaded (the reached bitmasks by ballot over the mask bytes, depths and colors of the
+// reached pixels; each warp takes four 32-pixel words at a time, their loads issued
+// before any is used), then filled exactly as the fused kernel fills its bands.  VAR as
+// in the fused kernel: false compiles the paper's kernel shape as constants.
+template <int NT, bool VAR>
 __global__ void __launch_bounds__(NT, 1) fill_only(FrameArgs f, const float* __restrict__ zt, int wpad)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     constexpr int NW = NT / 32;
     int *ctr, *rowinfo;
-    const KernelShape<true> ks(f);
+    const KernelShape<VAR> ks(f);
     Window s = window_layout(smem_raw, f.band + 2 * ks.halo, wpad, f.w, ctr, rowinfo);
     const int w = f.w, h = f.h, nwords = s.nwords;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -732,21 +734,38 @@ __global__ void __launch_bounds__(NT, 1) fill_only(FrameArgs f, const float* __r
         const int ra = max(y0 - ks.halo, 0), rb = min(y1 - 1 + ks.halo, h - 1);
         const int nr = rb - ra + 1;
         s.ra = ra;
-        for (int it = warp; it < nr * nwords; it += NW) {
-            const int j = it / nwords, g = it - j * nwords;
-            const int x = (g << 5) + lane;
-            const size_t o = (size_t)(ra + j) * w + x;
-            const bool reached = x < w && f.mask[o] == 0;
-            const uint32_t m = __ballot_sync(0xffffffffu, reached);
-            if (lane == 0 && YORO_BOUND(j < s.slots, kBadHoles)) s.bits[j * nwords + g] = m;
-            if (reached && YORO_BOUND(j * wpad + x < s.slots * wpad, kBadHoles)) {
-                s.zt[j * wpad + x] = __float_as_uint(zt[o]);
-                s.rgba[j * wpad + x] = f.out[o];
+        const int items = nr * nwords;
+        for (int it0 = warp; it0 < items; it0 += 4 * NW) {
+            uint32_t mk[4], zv[4], cv[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int it = it0 + q * NW;
+                const int j = it / nwords, g = it - j * nwords;
+                const int x = (g << 5) + lane;
+                const size_t o = (size_t)(ra + j) * w + x;
+                const bool ld = it < items && x < w;
+                mk[q] = ld ? f.mask[o] : 1u;
+                zv[q] = ld ? __float_as_uint(zt[o]) : 0u;
+                cv[q] = ld ? f.out[o] : 0u;
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int it = it0 + q * NW;
+                if (it >= items) break;  // warp-uniform
+                const int j = it / nwords, g = it - j * nwords;
+                const int x = (g << 5) + lane;
+                const bool reached = mk[q] == 0u;
+                const uint32_t m = __ballot_sync(0xffffffffu, reached);
+                if (lane == 0 && YORO_BOUND(j < s.slots, kBadHoles)) s.bits[j * nwords + g] = m;
+                if (reached && YORO_BOUND(j * wpad + x < s.slots * wpad, kBadHoles)) {
+                    s.zt[j * wpad + x] = zv[q];
+                    s.rgba[j * wpad + x] = cv[q];
+                }
             }
         }
         if (threadIdx.x == 0) *ctr = 0;
         __syncthreads();
-        fill_band<NT, true>(f, y0, y1, s, ctr, rowinfo);
+        fill_band<NT, VAR>(f, y0, y1, s, ctr, rowinfo);
     }
 }
 
@@ -944,7 +963,8 @@ cudaError_t fused_configure(int device, FusedLimits* lim)
                          (const void*)fused_single<kBig, 1, false, true>, (const void*)fused_single<kSmall, 2, false, true>,
                          (const void*)fused_batch<kBig, 1>,         (const void*)fused_batch<kSmall, 2>,
                          (const void*)fused_batch<kBig, 1, true>,   (const void*)fused_batch<kSmall, 2, true>,
-                         (const void*)fill_only<kBig>,              (const void*)imb_band<kBig>};
+                         (const void*)fill_only<kBig, false>,       (const void*)fill_only<kBig, true>,
+                         (const void*)imb_band<kBig>};
     for (const void* fn : fns) {
         e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
         if (e != cudaSuccess) return e;
@@ -1067,7 +1087,8 @@ cudaError_t fill_only_launch(FrameArgs f, const float* zt, const FusedLimits& li
     const int nbands = (f.h + f.band - 1) / f.band;
     const int grid = nbands < lim.sms ? nbands : lim.sms;
     if (grid < 1) return cudaSuccess;
-    fill_only<kBig><<<grid, kBig, smem, stream>>>(f, zt, wpad);
+    if (f.halo == 1 && !f.nearest) fill_only<kBig, false><<<grid, kBig, smem, stream>>>(f, zt, wpad);
+    else fill_only<kBig, true><<<grid, kBig, smem, stream>>>(f, zt, wpad);
     return cudaGetLastError();
 }
 
