@@ -769,6 +769,74 @@ __global__ void __launch_bounds__(NT, 1) fill_only(FrameArgs f, const float* __r
     }
 }
 
+// The band fill straight from a frame-wide z-buffer of 64-bit keys (clamped depth bits
+// above the source pixel's index, the empty key at holes: the general pose's Alg. 2 over
+// the frame): each band's window is loaded from the keys (reached bitmask, the depth from
+// the key, the winner's color gathered from f.color), the band rows' colors of reached
+// pixels and their hole mask leave for global memory, and the holes are filled as in
+// fill_only.  It stands in for a gather pass that writes the image out and fill_only's
+// reading it back.
+template <int NT, bool VAR>
+__global__ void __launch_bounds__(NT, 1) fill_keys(FrameArgs f, const unsigned long long* __restrict__ keys, int wpad)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    constexpr int NW = NT / 32;
+    int *ctr, *rowinfo;
+    const KernelShape<VAR> ks(f);
+    Window s = window_layout(smem_raw, f.band + 2 * ks.halo, wpad, f.w, ctr, rowinfo);
+    const int w = f.w, h = f.h, nwords = s.nwords;
+    const size_t n = (size_t)w * (size_t)h;  // source indices are below n (checked in the debug-bounds build)
+    (void)n;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nbands = (h + f.band - 1) / f.band;
+    for (int b = blockIdx.x; b < nbands; b += gridDim.x) {
+        const int y0 = b * f.band, y1 = min(y0 + f.band, h);
+        const int ra = max(y0 - ks.halo, 0), rb = min(y1 - 1 + ks.halo, h - 1);
+        const int nr = rb - ra + 1;
+        s.ra = ra;
+        const int items = nr * nwords;
+        for (int it0 = warp; it0 < items; it0 += 4 * NW) {
+            unsigned long long kv[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int it = it0 + q * NW;
+                const int j = it / nwords, g = it - j * nwords;
+                const int x = (g << 5) + lane;
+                kv[q] = (it < items && x < w) ? keys[(size_t)(ra + j) * w + x] : kEmptyKey;
+            }
+            uint32_t cv[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const uint32_t src = (uint32_t)kv[q];
+                cv[q] = (kv[q] != kEmptyKey && YORO_BOUND(src < n, kBadPose)) ? __ldg(f.color + src) : 0u;
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int it = it0 + q * NW;
+                if (it >= items) break;  // warp-uniform
+                const int j = it / nwords, g = it - j * nwords;
+                const int x = (g << 5) + lane;
+                const bool reached = kv[q] != kEmptyKey;
+                const uint32_t m = __ballot_sync(0xffffffffu, reached);
+                if (lane == 0 && YORO_BOUND(j < s.slots, kBadHoles)) s.bits[j * nwords + g] = m;
+                if (reached && YORO_BOUND(j * wpad + x < s.slots * wpad, kBadHoles)) {
+                    s.zt[j * wpad + x] = (uint32_t)(kv[q] >> 32);
+                    s.rgba[j * wpad + x] = cv[q];
+                }
+                const int v = ra + j;
+                if (v >= y0 && v < y1 && x < w) {  // a band row: the pixel and its mask byte leave
+                    const size_t o = (size_t)v * w + x;
+                    if (reached) f.out[o] = cv[q];
+                    f.mask[o] = reached ? 0 : 1;
+                }
+            }
+        }
+        if (threadIdx.x == 0) *ctr = 0;
+        __syncthreads();
+        fill_band<NT, VAR>(f, y0, y1, s, ctr, rowinfo);
+    }
+}
+
 // The row-downsampled intermediate buffer in one kernel: per band, the window rows'
 // cells are reprojected into 64-bit cell keys in shared memory (after the window),
 // every window pixel is sampled from its cell's winner into the window (depth, color,
@@ -964,6 +1032,7 @@ cudaError_t fused_configure(int device, FusedLimits* lim)
                          (const void*)fused_batch<kBig, 1>,         (const void*)fused_batch<kSmall, 2>,
                          (const void*)fused_batch<kBig, 1, true>,   (const void*)fused_batch<kSmall, 2, true>,
                          (const void*)fill_only<kBig, false>,       (const void*)fill_only<kBig, true>,
+                         (const void*)fill_keys<kBig, false>,       (const void*)fill_keys<kBig, true>,
                          (const void*)imb_band<kBig>};
     for (const void* fn : fns) {
         e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
@@ -1089,6 +1158,21 @@ cudaError_t fill_only_launch(FrameArgs f, const float* zt, const FusedLimits& li
     if (grid < 1) return cudaSuccess;
     if (f.halo == 1 && !f.nearest) fill_only<kBig, false><<<grid, kBig, smem, stream>>>(f, zt, wpad);
     else fill_only<kBig, true><<<grid, kBig, smem, stream>>>(f, zt, wpad);
+    return cudaGetLastError();
+}
+
+cudaError_t fill_keys_launch(FrameArgs f, const unsigned long long* keys, const FusedLimits& lim, cudaStream_t stream)
+{
+    const int wpad = fused_wpad(f.w);
+    // bands as tall as shared memory allows, but at least one per SM
+    const int per_sm = (f.h + lim.sms - 1) / lim.sms;
+    f.band = max(1, min(max_band(lim, wpad, f.halo), per_sm));
+    const size_t smem = fused_smem_bytes(wpad, f.band, f.halo);
+    const int nbands = (f.h + f.band - 1) / f.band;
+    const int grid = nbands < lim.sms ? nbands : lim.sms;
+    if (grid < 1) return cudaSuccess;
+    if (f.halo == 1 && !f.nearest) fill_keys<kBig, false><<<grid, kBig, smem, stream>>>(f, keys, wpad);
+    else fill_keys<kBig, true><<<grid, kBig, smem, stream>>>(f, keys, wpad);
     return cudaGetLastError();
 }
 

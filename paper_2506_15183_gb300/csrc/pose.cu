@@ -12,8 +12,9 @@
 //      y w + x on equal depth: a 64-bit atomicMin of (p'.z bits << 32 | index).
 //   3. Gather: the winner's color; p'.z is the target's depth.
 //   4. Holes along each row and the Patcher (Alg. 3, Eq. 6) over the gathered image:
-//      the fused kernel's band fill (fill_only in fused.cu) when a band fits shared
-//      memory, else one thread per hole pixel.
+//      when a band fits shared memory, the fused kernel's band fill reading the keys
+//      itself (fill_keys in fused.cu: steps 3 and 4 in one kernel), else a gather pass
+//      and one thread per hole pixel.
 // Every float operation is an explicit round-to-nearest intrinsic (IEEE division
 // included), never contracted, so the result equals the oracle's byte for byte.
 #include <cuda_runtime.h>
@@ -109,9 +110,10 @@ cudaError_t pose_launch(const FrameArgs& f, const PoseArgs& p, const FusedLimits
     const int threads = 256;
     pose_scatter_kernel<<<blocks_for(n, threads), threads, 0, stream>>>(f, p);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    // a band fits shared memory: the band fill reads the keys itself (gather included)
+    if (band_fill) return fill_keys_launch(f, p.zbuf, lim, stream);
     pose_gather_kernel<<<blocks_for(n, threads), threads, 0, stream>>>(f, p);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if (band_fill) return fill_only_launch(f, p.zt, lim, stream);
     return fill_pixels_launch(f, p.zt, stream);
 }
 

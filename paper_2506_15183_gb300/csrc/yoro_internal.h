@@ -114,6 +114,10 @@ cudaError_t imb_launch(const FrameArgs& f, const ImbArgs& a, const FusedLimits& 
 // The fused kernel's hole fill (P3) over a frame resolved in global memory: reached
 // colors in f.out, their depths in zt, the hole mask in f.mask.
 cudaError_t fill_only_launch(FrameArgs f, const float* zt, const FusedLimits& lim, cudaStream_t stream);
+// The same fill read straight from a frame-wide z-buffer of 64-bit keys (depth bits above
+// the source index, ~0 at holes): also writes the reached pixels' colors (gathered from
+// f.color) and the hole mask.
+cudaError_t fill_keys_launch(FrameArgs f, const unsigned long long* keys, const FusedLimits& lim, cudaStream_t stream);
 // The holes of a frame resolved in global memory (colors in f.out, depths in zt, mask
 // in f.mask), one thread per pixel: for frames too wide for a band window.
 cudaError_t fill_pixels_launch(const FrameArgs& f, const float* zt, cudaStream_t stream);
