@@ -471,7 +471,12 @@ __global__ void __launch_bounds__(128, 1)
                 issue(kk, n0, y0);
             }
         } else if (warp == 1 && lane == 0) {  // MMAs
+            // Descriptors: a stage's bases plus constants in the 16-byte start-address
+            // field (the smem window is below 256 KB, so the field never carries over).
             const uint32_t idesc = idesc_bf16(a.Cout);
+            const uint64_t dbase = desc_sw64(smem_u32(smem));
+            const uint32_t aW = (uint32_t)a.W * 4u, aT = (uint32_t)kTileM * 4u, bT = (uint32_t)b_tap >> 4;
+            const uint32_t d1 = tmem + (uint32_t)a.Cout;
             for (int k = 0; k < nk; ++k) {
                 const int kk = it * nk + k, s = kk % S;
                 if (!mbar_wait(&full[s], (kk / S) & 1, deadline)) {
@@ -480,15 +485,17 @@ __global__ void __launch_bounds__(128, 1)
                     break;
                 }
                 tc_fence_after();
-                const uint32_t sa = smem_u32(smem + s * stage_bytes), sb = sa + a_span;
+                const uint64_t da = dbase + (uint64_t)((uint32_t)(s * stage_bytes) >> 4);
+                const uint64_t db = da + (uint64_t)((uint32_t)a_span >> 4);
+#pragma unroll
                 for (int dy = 0; dy < 3; ++dy) {
-                    const uint32_t bt = sb + dy * b_tap;
-                    for (int j = 0; j < mt; ++j) {
-                        const uint32_t at = sa + (uint32_t)(j * kTileM + dy * a.W) * (kKc * 2);
-                        const uint32_t d = tmem + (uint32_t)(j * a.Cout);
-                        mma_bf16(d, desc_sw64(at), desc_sw64(bt), idesc, (k > 0 || dy > 0) ? 1u : 0u);
-                        mma_bf16(d, desc_sw64(at + 32), desc_sw64(bt + 32), idesc, 1u);
-                    }
+                    const uint64_t bt = db + dy * bT;
+                    const uint64_t a0 = da + dy * aW, a1 = a0 + aT;
+                    const uint32_t acc = (k > 0 || dy > 0) ? 1u : 0u;
+                    mma_bf16(tmem, a0, bt, idesc, acc);
+                    mma_bf16(tmem, a0 + 2, bt + 2, idesc, 1u);
+                    mma_bf16(d1, a1, bt, idesc, acc);
+                    mma_bf16(d1, a1 + 2, bt + 2, idesc, 1u);
                 }
                 mma_commit(&empty[s]);
                 counts[1] = kk + 1;
