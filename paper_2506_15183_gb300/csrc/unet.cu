@@ -456,12 +456,16 @@ __global__ void __launch_bounds__(128, 1)
     // The CTA walks bands blockIdx.x, + gridDim.x, ...: per band its K steps, then the
     // epilogue; the barriers' phases run on across bands (step kk of the walk), and the
     // accumulators are reused once every thread's reads of them are done.
+    // Where a band's output fits one stage, the epilogue stages it in the stage of the
+    // band's last K step, and the next band's first copy (into the other stage, free
+    // since the MMAs completed) is issued before the epilogue, so it lands meanwhile.
+    const bool early = mt * kTileM * a.Cout * 2 <= stage_bytes && S >= 2;
     int it = 0;
     for (int band = blockIdx.x; band < live; band += gridDim.x, ++it) {
         const int n0 = band / bands_per_tile, y0 = (band - n0 * bands_per_tile) * R;
         const uint64_t deadline = globaltimer() + kWaitNs;
         if (warp == 0 && lane == 0) {  // copies
-            for (int k = it == 0 ? first : 0; k < nk; ++k) {
+            for (int k = it == 0 ? first : (early ? 1 : 0); k < nk; ++k) {
                 const int kk = it * nk + k, s = kk % S;
                 if (!mbar_wait(&empty[s], ((kk / S) & 1) ^ 1, deadline)) {
                     atomicOr(&g_unet_status, kUnetTimeout);
@@ -510,9 +514,21 @@ __global__ void __launch_bounds__(128, 1)
         }
         __syncthreads();
         const bool go = ok && !counts[2];  // the same for every thread (read after the barrier)
+        const int next = band + (int)gridDim.x;
+        if (go && early && next < live && threadIdx.x == 0) {  // the next band's first copy
+            const int kk = (it + 1) * nk, s = kk % S;
+            const int n1 = next / bands_per_tile, y1 = (next - n1 * bands_per_tile) * R;
+            if (mbar_wait(&empty[s], ((kk / S) & 1) ^ 1, deadline)) issue(kk, n1, y1);
+            else {
+                atomicOr(&g_unet_status, kUnetTimeout);
+                counts[2] = 1;
+            }
+        }
         if (go) {
             tc_fence_after();
-            epilogue_store(a, &tmY, tmem, smem, sbias, mt, n0, y0);
+            // early: the stage of this band's last K step (its copies were consumed)
+            unsigned char* stg = early ? smem + ((it * nk + nk - 1) % S) * stage_bytes : smem;
+            epilogue_store(a, &tmY, tmem, stg, sbias, mt, n0, y0);
         }
         // every thread's reads of the accumulators are done before the next band's MMAs
         tc_fence_before();
