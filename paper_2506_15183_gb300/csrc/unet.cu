@@ -457,8 +457,9 @@ __global__ void __launch_bounds__(128, 1)
     // epilogue; the barriers' phases run on across bands (step kk of the walk), and the
     // accumulators are reused once every thread's reads of them are done.
     // Where a band's output fits one stage, the epilogue stages it in the stage of the
-    // band's last K step, and the next band's first copy (into the other stage, free
-    // since the MMAs completed) is issued before the epilogue, so it lands meanwhile.
+    // band's last K step, and the next band's first copy (into the other stage) is issued
+    // by the MMA thread once that stage is free, so it lands during the last MMAs and the
+    // epilogue.
     const bool early = mt * kTileM * a.Cout * 2 <= stage_bytes && S >= 2;
     int it = 0;
     for (int band = blockIdx.x; band < live; band += gridDim.x, ++it) {
@@ -505,6 +506,18 @@ __global__ void __launch_bounds__(128, 1)
                 counts[1] = kk + 1;
             }
             mma_commit(done);  // arrives once every MMA issued above has completed
+            // early: the next band's first copy, into the stage the second-to-last K step
+            // frees, while this band's last MMAs run
+            const int next = band + (int)gridDim.x;
+            if (early && next < live && !counts[2]) {
+                const int kk = (it + 1) * nk, s = kk % S;
+                const int n1 = next / bands_per_tile, y1 = (next - n1 * bands_per_tile) * R;
+                if (mbar_wait(&empty[s], ((kk / S) & 1) ^ 1, deadline)) issue(kk, n1, y1);
+                else {
+                    atomicOr(&g_unet_status, kUnetTimeout);
+                    counts[2] = 1;
+                }
+            }
         }
         __syncwarp();
         const bool ok = mbar_wait(done, it & 1, deadline + kWaitNs);
@@ -514,16 +527,6 @@ __global__ void __launch_bounds__(128, 1)
         }
         __syncthreads();
         const bool go = ok && !counts[2];  // the same for every thread (read after the barrier)
-        const int next = band + (int)gridDim.x;
-        if (go && early && next < live && threadIdx.x == 0) {  // the next band's first copy
-            const int kk = (it + 1) * nk, s = kk % S;
-            const int n1 = next / bands_per_tile, y1 = (next - n1 * bands_per_tile) * R;
-            if (mbar_wait(&empty[s], ((kk / S) & 1) ^ 1, deadline)) issue(kk, n1, y1);
-            else {
-                atomicOr(&g_unet_status, kUnetTimeout);
-                counts[2] = 1;
-            }
-        }
         if (go) {
             tc_fence_after();
             // early: the stage of this band's last K step (its copies were consumed)
