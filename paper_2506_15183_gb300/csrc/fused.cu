@@ -289,18 +289,6 @@ __device__ __forceinline__ int nth_set_bit(uint32_t m, int k)
     return pos;
 }
 
-// Next item of a flat (row, column) enumeration dealt round-robin: advance by `dq`
-// columns and `dr` rows (the stride split as rows and a remainder), carrying a row.
-__device__ __forceinline__ void advance(int& r, int& q, int dr, int dq, int n)
-{
-    q += dq;
-    r += dr;
-    if (q >= n) {
-        q -= n;
-        ++r;
-    }
-}
-
 // P1 (Alg. 1 closed form, Alg. 2 nearest kept) over the window's nr rows.
 //
 // Alg. 2 keeps, per target, the nearest source, on equal depth the one met first.  In
@@ -314,14 +302,65 @@ __device__ __forceinline__ void advance(int& r, int& q, int dr, int dq, int n)
 // its target's word (one native 32-bit shared atomic), and the depth is fetched for
 // the winner alone in P2.
 //
-// The window's rows are contiguous in memory, so its pixels are enumerated in memory
-// order and dealt round-robin over the threads (consecutive lanes, consecutive
-// columns); each thread issues the loads of U = 4 pixels before it processes any (8
-// and 2 were measured slower).  The groups whose U loads are all in range run without
-// per-pixel range tests; one remainder group keeps them.
+// Two forms deal the window's pixels to the threads.  In the two-column form each
+// thread takes the columns x = tid and x + NT of every window row: consecutive lanes take
+// consecutive columns, so a warp's loads of one row are one 128-byte line; a column's
+// centre x + 0.5 and its depth pointer are set once, so a pixel costs only its row step;
+// and the thread issues the loads of U = 5 rows of both columns before it processes any
+// (a 15-row window is three groups; the rows left over form one group of their own
+// height).  At 1832 columns it executes 12 % fewer
+// instructions than the flat form below and keeps more loads in flight (measured
+// against one column at a time with 3 to 15 rows per group, two columns with 3, 4 or 7
+// rows, and (row group, column) units dealt round-robin).  But a thread's share is whole
+// columns, so where the columns do not split evenly over the threads the flat form,
+// pixels dealt round-robin in memory order, balances better.
+template <int NT, int U>
+__device__ __forceinline__ void scatter_rows(const FrameArgs& f, const float* dcol, int j, int nr, int x, float xc,
+                                             bool two, int* srow, int wpad, uint32_t near_m1, uint32_t far_m1)
+{
+    const int w = f.w;
+    float z[2][U];
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            z[c][u] = ((c == 0 || two) && YORO_BOUND(j + u < nr, kBadScatter))
+                          ? __ldg(dcol + c * NT + (size_t)u * w)
+                          : 0.0f;
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (c == 0 || two) {
+                uint32_t zb;
+                const int xt = disparity_target(z[c][u], __fadd_rn(xc, (float)(c * NT)), f.k, near_m1, far_m1,
+                                                f.half_m, zb);
+                if ((unsigned)xt < (unsigned)w && YORO_BOUND(j + u < nr, kBadScatter))
+                    atomicMax(srow + u * wpad + xt, x + c * NT);
+            }
+        }
+}
+
+// Next pixel of a flat (row, column) enumeration of a region `rw` columns wide dealt
+// round-robin: advance by `dq` columns and `dr` rows (the stride split as rows and a
+// remainder), carrying a row.
+__device__ __forceinline__ void advance(int& r, int& q, int dr, int dq, int rw)
+{
+    q += dq;
+    r += dr;
+    if (q >= rw) {
+        q -= rw;
+        ++r;
+    }
+}
+
+// The flat form over columns x0 .. w-1 of the window rows: pixel i = r * rw + q
+// (rw = w - x0) goes to thread i mod NT, which issues the loads of U = 4 pixels before
+// it processes any.
 template <int NT, int U, bool FULL>
-__device__ __forceinline__ void scatter_iter(const FrameArgs& f, const float* depth, int n, int i, int& r, int& q,
-                                             int dr, int dq, int* src, int wpad, uint32_t near_m1, uint32_t far_m1)
+__device__ __forceinline__ void scatter_flat(const FrameArgs& f, const float* depth, int n, int i, int& r, int& q,
+                                             int dr, int dq, int x0, int rw, int* src, int wpad, uint32_t near_m1,
+                                             uint32_t far_m1)
 {
     const int w = f.w;
     float z[U];
@@ -329,18 +368,18 @@ __device__ __forceinline__ void scatter_iter(const FrameArgs& f, const float* de
 #pragma unroll
     for (int u = 0; u < U; ++u) {
         ru[u] = r;
-        xu[u] = q;
-        z[u] = ((FULL || i + u * NT < n) && YORO_BOUND(i + u * NT < n, kBadScatter)) ? __ldg(depth + i + u * NT)
-                                                                                        : 0.0f;
-        advance(r, q, dr, dq, w);
+        xu[u] = x0 + q;
+        z[u] = ((FULL || i + u * NT < n) && YORO_BOUND(i + u * NT < n, kBadScatter))
+                   ? __ldg(depth + (size_t)r * w + x0 + q)
+                   : 0.0f;
+        advance(r, q, dr, dq, rw);
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
         if (FULL || i + u * NT < n) {
             uint32_t zb;
             const int xt = disparity_target(z[u], __fadd_rn((float)xu[u], 0.5f), f.k, near_m1, far_m1, f.half_m, zb);
-            if ((unsigned)xt < (unsigned)w && YORO_BOUND(ru[u] * w + xu[u] < n, kBadScatter))
-                atomicMax(src + ru[u] * wpad + xt, xu[u]);
+            if ((unsigned)xt < (unsigned)w) atomicMax(src + ru[u] * wpad + xt, xu[u]);
         }
     }
 }
@@ -348,16 +387,46 @@ __device__ __forceinline__ void scatter_iter(const FrameArgs& f, const float* de
 template <int NT>
 __device__ __forceinline__ void scatter_window(const FrameArgs& f, const float* depth, int nr, int* src, int wpad)
 {
-    constexpr int U = 4;
+    constexpr int U = 5;
     const int w = f.w;
-    const int n = nr * w;
     const uint32_t near_m1 = __float_as_uint(f.near_) - 1u, far_m1 = __float_as_uint(f.far_) - 1u;
-    const int dr = NT / w, dq = NT - dr * w;
-    int r = (int)threadIdx.x / w, q = (int)threadIdx.x - r * w;
-    int i = threadIdx.x;
-    for (; i + (U - 1) * NT < n; i += U * NT)  // every load of the group in range
-        scatter_iter<NT, U, true>(f, depth, n, i, r, q, dr, dq, src, wpad, near_m1, far_m1);
-    if (i < n) scatter_iter<NT, U, false>(f, depth, n, i, r, q, dr, dq, src, wpad, near_m1, far_m1);
+    // Columns of the two-column form: the first 2 NT of a frame at least that wide, else
+    // all of them if no thread's share exceeds the mean share by more than a quarter
+    // (2 NT / w or NT / w <= 5/4; at 1440 columns, 2 NT / w = 1.42 and the flat form
+    // measured 3 % faster), else none.
+    const int pc = w >= 2 * NT ? 2 * NT : (w > NT ? (5 * w >= 8 * NT ? w : 0) : (5 * w >= 4 * NT ? w : 0));
+    const int x = threadIdx.x;
+    if (x < pc) {
+        const bool two = x + NT < pc;
+        const float xc = __fadd_rn((float)x, 0.5f);  // exact: x < 2^23
+        const float* dcol = depth + x;
+        int* srow = src;
+        int j = 0;
+        for (; j + U <= nr; j += U) {  // every row of the group in the window
+            scatter_rows<NT, U>(f, dcol, j, nr, x, xc, two, srow, wpad, near_m1, far_m1);
+            dcol += (size_t)U * w;
+            srow += U * wpad;
+        }
+        switch (nr - j) {  // the last rows as one group of their own height
+        case 1: scatter_rows<NT, 1>(f, dcol, j, nr, x, xc, two, srow, wpad, near_m1, far_m1); break;
+        case 2: scatter_rows<NT, 2>(f, dcol, j, nr, x, xc, two, srow, wpad, near_m1, far_m1); break;
+        case 3: scatter_rows<NT, 3>(f, dcol, j, nr, x, xc, two, srow, wpad, near_m1, far_m1); break;
+        case 4: scatter_rows<NT, 4>(f, dcol, j, nr, x, xc, two, srow, wpad, near_m1, far_m1); break;
+        default: break;
+        }
+    }
+    // the other columns (none at 1832 columns; 16 at 2064) in the flat form
+    const int rw = w - pc;
+    if (rw > 0) {
+        constexpr int UF = 4;
+        const int n = nr * rw;
+        const int dr = NT / rw, dq = NT - dr * rw;
+        int r = (int)threadIdx.x / rw, q = (int)threadIdx.x - r * rw;
+        int i = threadIdx.x;
+        for (; i + (UF - 1) * NT < n; i += UF * NT)  // every load of the group in range
+            scatter_flat<NT, UF, true>(f, depth, n, i, r, q, dr, dq, pc, rw, src, wpad, near_m1, far_m1);
+        if (i < n) scatter_flat<NT, UF, false>(f, depth, n, i, r, q, dr, dq, pc, rw, src, wpad, near_m1, far_m1);
+    }
 }
 
 // P2 (resolve + gather) over the window: warp `warp` owns the 32-pixel words

@@ -52,9 +52,10 @@ __device__ __forceinline__ uint32_t clamped_depth_bits(float z, uint32_t near_m1
 // writes the bits of the clamped depth.  `xc` is the pixel centre x + 0.5.
 //
 // Only the floor is needed, so the IEEE quotient is computed only when a cheaper
-// estimate cannot decide it.  With q = RN(k * rcp(zc)), |q - k/zc| <= 1.51 * 2^-23 k/zc
-// and |q - RN(k/zc)| <= 2.01 * 2^-23 k/zc; adding the two roundings of the subtraction,
-// t' = RN(xc - q) is within 2^-21 (xc + q) of t = RN(xc - RN(k/zc)).  `half_m` is
+// estimate cannot decide it.  With Q = k/zc and r = rcp(zc) (|r - 1/zc| <= 2^-23 / zc),
+// the estimate t' = RN(xc - k * r), one fused multiply-add, is within
+// 2^-23 Q + 2^-24 (xc + Q) (1 + 2^-23) of xc - Q, and t = RN(xc - RN(Q)) within
+// 2^-24 Q + 2^-24 (xc + Q) (1 + 2^-24); so |t' - t| < 2^-21 (xc + Q).  `half_m` is
 // 0.5 - M with M = 2^-20 (w + 1.5 + k/near) * (1 + 2^-10) >= twice that distance plus
 // an absolute 2^-20 (which also covers flushed denormals), bounded on the host per
 // frame.  If frac(t') lies in (M, 1 - M), floor(t) == floor(t').
@@ -63,7 +64,7 @@ __device__ __forceinline__ int disparity_target(float z, float xc, float k, uint
 {
     zbits = clamped_depth_bits(z, near_m1, far_m1);
     const float zc = __uint_as_float(zbits);
-    const float tp = __fsub_rn(xc, __fmul_rn(k, rcp_approx(zc)));
+    const float tp = __fmaf_rn(-k, rcp_approx(zc), xc);
     const float fl = floorf(tp);
     if (fabsf(__fsub_rn(__fsub_rn(tp, fl), 0.5f)) < half_m) return (int)fl;
     return exact_target(xc, k, zc);

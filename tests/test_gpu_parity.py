@@ -230,6 +230,17 @@ def test_max_fused_width_and_beyond(yoro):
         _assert_same(_run(yoro, c, d, cam), _ref(c, d, cam), f"width {w}")
 
 
+def test_widths_around_the_scatter_column_split(yoro):
+    """The scatter's two forms: whole columns per thread (x and x + 1024) where they
+    split evenly enough over the 1024 threads, pixels dealt round-robin elsewhere and
+    past column 2048: widths on either side of each switch."""
+    for w in (800, 820, 1023, 1024, 1025, 1638, 1639, 2047, 2048, 2049, 2100, 2300):
+        h = 29
+        c, d = _random_frame(h, w, seed=w + 7, zlo=0.1, zhi=10.0)
+        cam = _cam(w, h, ipd=0.08)
+        _assert_same(_run(yoro, c, d, cam), _ref(c, d, cam), f"width {w}")
+
+
 def test_empty_frames(yoro):
     for w, h in ((0, 0), (0, 5), (5, 0)):
         hdl = yoro.yoro_create(**_cam(max(w, 1), h) | dict(w=w, h=h))
