@@ -718,6 +718,11 @@ def main():
         if world > 1:
             torch.distributed.barrier()
 
+    # the clock sampler starts first (nvidia-smi takes a moment to begin sampling), so that
+    # the warm-up runs right before the timed region and the GPU does not idle between them
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
     # warm-up
     for i in range(args.warmup):
         rc = step(i)
@@ -725,20 +730,24 @@ def main():
             raise yoro.YoroError(rc, "yoro_synthesize")
     torch.cuda.synchronize(device)
 
-    # timed region: K back-to-back frames on one stream
-    clocks = ClockSampler(local)
-    clocks.start()
-    time.sleep(0.3)
+    # timed region: K back-to-back frames dealt round-robin over the streams
     barrier()
     torch.cuda.synchronize(device)
-    # every stream waits for ev0 and ev1 waits for every stream, so [ev0, ev1] spans all K steps
+    # every stream waits for ev0 before its first step and ev1 waits for every stream, so
+    # [ev0, ev1] spans all K steps; each wait is issued just before its stream's first step,
+    # so the first frame is queued right after ev0
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
-    for st in streams[1:]:
-        st.wait_event(ev0)
+    waiting = set(range(1, nstreams))
     for i in range(args.steps):
+        k = i % nstreams
+        if k in waiting:
+            streams[k].wait_event(ev0)
+            waiting.discard(k)
         step(i)
+    for k in waiting:
+        streams[k].wait_event(ev0)
     for st in streams[1:]:
         done = torch.cuda.Event()
         done.record(st)
