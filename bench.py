@@ -840,12 +840,16 @@ def run_e2e(yoro, lib, cfg, pool, device, steps, warmup):
     t0 = time.perf_counter()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev0.record(streams[0])
-    for s in streams[1:]:
-        s.wait_event(ev0)
+    waiting = set(range(1, nslot))  # each stream waits for ev0 just before its first step
     for i in range(steps):
+        if i % nslot in waiting:
+            streams[i % nslot].wait_event(ev0)
+            waiting.discard(i % nslot)
         rc = fn(*calls[i % nslot])
         if rc:
             raise yoro.YoroError(rc, "yoro_synthesize_host")
+    for k in waiting:
+        streams[k].wait_event(ev0)
     ends = []
     for s in streams:
         e = torch.cuda.Event(enable_timing=True)
