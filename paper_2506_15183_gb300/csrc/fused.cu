@@ -13,15 +13,17 @@
 //       column into its target's word (O1: a row never writes another row).  In a
 //       row, of two sources that reach the same target the one further right is
 //       the nearer (see scatter_window), so the maximum column is the z-test's
-//       winner;
+//       winner.  A thread takes whole columns (two, five rows of each per load
+//       group) where they split evenly over the threads, else pixels round-robin;
 //   P2  resolve + gather: each reached target loads its source's depth and color;
 //       warp ballots write the rows' reached-pixel bitmasks, and the band rows'
 //       reached pixels and hole mask leave for global memory at once;
 //   P3a per band row: its last reached pixel, the border holes right of it (the
 //       fallback), and per word the counts of cracks and wider holes with prefix sums;
-//   P3b the other holes are filled (Alg. 3, Eq. 6) in chunks of 32 dealt to whichever
-//       warp is free, one hole per lane, so a wide disocclusion is spread over many
-//       warps; a chunk inside one hole is filled by the whole warp together.  Hole
+//   P3b the other holes are filled (Alg. 3, Eq. 6) in chunks dealt to whichever warp
+//       is free (32 pixels of wider holes, one per lane, or 64 one-pixel cracks, two
+//       per lane), so a wide disocclusion is spread over many warps; a chunk inside
+//       one hole is filled by the whole warp together.  Hole
 //       edges and kernel candidates come from the bitmasks (leading/trailing-zero
 //       counts over 32-pixel words).
 //
