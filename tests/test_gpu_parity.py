@@ -241,6 +241,51 @@ def test_widths_around_the_scatter_column_split(yoro):
         _assert_same(_run(yoro, c, d, cam), _ref(c, d, cam), f"width {w}")
 
 
+def _crack_frame(h, w, seed):
+    """Rows of one-pixel cracks: even columns at disparity D, odd ones at D - 1, so every
+    second target pixel is a crack (over the whole row, its left or its right part, or
+    nowhere), with the rows' crack counts odd and even so that cracks dealt two per lane
+    cross row ends."""
+    rng = np.random.default_rng(seed)
+    fx = w / 2.0
+    cam = _cam(w, h, fx=fx, ipd=0.08)
+    k = np.float32(fx) * np.float32(cam["ipd"])
+    d = np.empty((h, w), np.float32)
+    for y in range(h):
+        dd = rng.uniform(3.2, 9.7)
+        row = np.full(w, k / dd, np.float32)
+        kind = y % 4
+        if kind == 1:
+            row[1::2] = k / (dd - 1.0)
+        elif kind == 2:
+            row[1 : int(rng.integers(w // 4, 3 * w // 4)) : 2] = k / (dd - 1.0)
+        elif kind == 3:
+            row[int(rng.integers(w // 4, 3 * w // 4)) | 1 :: 2] = k / (dd - 1.0)
+        d[y] = row
+    c = rng.integers(0, 256, (h, w, 4), dtype=np.uint8)
+    return c, d, cam
+
+
+def test_crack_dense_frames(yoro):
+    """Thousands of one-pixel cracks per band (the fill deals them two per lane), single
+    frames and one batched launch, byte for byte against the oracle."""
+    frames, refs = [], []
+    for h, w, seed in ((41, 301, 1), (64, 1832, 2), (29, 1024, 3)):
+        c, d, cam = _crack_frame(h, w, seed)
+        ref = _ref(c, d, cam)
+        assert int(ref[1].sum()) > h * w // 5  # mostly cracks
+        _assert_same(_run(yoro, c, d, cam), ref, f"cracks {w}x{h}")
+        refs.append(ref)
+        frames.append(dict(cam, color=torch.from_numpy(c).to(DEV), depth=torch.from_numpy(d).to(DEV),
+                           out_color=torch.empty((h, w, 4), dtype=torch.uint8, device=DEV),
+                           out_mask=torch.empty((h, w), dtype=torch.uint8, device=DEV)))
+    yoro.yoro_synthesize_batch(frames)
+    torch.cuda.synchronize()
+    assert yoro.yoro_stream_status(None) == 0
+    for fr, ref in zip(frames, refs):
+        _assert_same((fr["out_color"].cpu().numpy(), fr["out_mask"].cpu().numpy()), ref, f"batch cracks {fr['w']}")
+
+
 def test_empty_frames(yoro):
     for w, h in ((0, 0), (0, 5), (5, 0)):
         hdl = yoro.yoro_create(**_cam(max(w, 1), h) | dict(w=w, h=h))
