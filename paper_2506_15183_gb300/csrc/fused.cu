@@ -511,7 +511,12 @@ __device__ __forceinline__ void resolve_batch(const FrameArgs& f, const float* d
     }
 }
 
-template <int NT, bool ZT>
+// WIDE (windows wider than 2 NT words): the words from 2 NT on are dealt as (word, row
+// batch) items over all warps instead of as a third word of the first warps (2064-wide
+// frames: 29.0 -> 27.5 us per frame).  A separate instantiation, so that the code of the
+// common width is untouched (compiled into one kernel the extra loop cost 1832-wide
+// frames 2.5 %).
+template <int NT, bool ZT, bool WIDE = false>
 __device__ __forceinline__ void resolve_window(const FrameArgs& f, const float* depth, const uint32_t* color,
                                                int nr, int y0, int y1, const Window& s)
 {
@@ -520,7 +525,7 @@ __device__ __forceinline__ void resolve_window(const FrameArgs& f, const float* 
     const int warp = threadIdx.x >> 5;
     const uint32_t near_m1 = __float_as_uint(f.near_) - 1u, far_m1 = __float_as_uint(f.far_) - 1u;
     const int jb0 = y0 - s.ra, jb1 = y1 - s.ra;  // band rows of the window: [jb0, jb1)
-    for (int g = warp; g < s.nwords; g += 2 * NW) {
+    for (int g = warp; g < (WIDE ? min(s.nwords, 2 * NW) : s.nwords); g += 2 * NW) {
         const bool two = g + NW < s.nwords;  // warp-uniform
         int j0 = 0;
         for (; j0 + RB <= nr; j0 += RB) {
@@ -534,6 +539,17 @@ __device__ __forceinline__ void resolve_window(const FrameArgs& f, const float* 
                                                      far_m1);
         }
     }
+    if (WIDE) {
+        const int nbat = (nr + RB - 1) / RB;
+        for (int it = warp; it < (s.nwords - 2 * NW) * nbat; it += NW) {
+            const int gw = 2 * NW + it / nbat, j0 = (it - (it / nbat) * nbat) * RB;
+            if (j0 + RB <= nr)
+                resolve_batch<RB, true, 1, DX, ZT>(f, depth, color, s, gw, j0, RB, nr, jb0, jb1, near_m1, far_m1);
+            else
+                resolve_batch<RB, false, 1, DX, ZT>(f, depth, color, s, gw, j0, nr - j0, nr, jb0, jb1, near_m1,
+                                                    far_m1);
+        }
+    }
 }
 
 // One band [y0, y1) of one frame; shared memory holds the window rows ra..rb
@@ -543,7 +559,7 @@ template <int NT, bool VAR>
 __device__ __forceinline__ void fill_band(const FrameArgs& f, int y0, int y1, const Window& s, int* ctr,
                                           int* rowinfo);
 
-template <int NT, bool VAR, bool ZT>
+template <int NT, bool VAR, bool ZT, bool WIDE = false>
 __device__ __forceinline__ void run_band(const FrameArgs& f, int y0, int y1, Window s, int* ctr, int* rowinfo)
 {
     constexpr int NW = NT / 32;
@@ -577,7 +593,7 @@ __device__ __forceinline__ void run_band(const FrameArgs& f, int y0, int y1, Win
 
     // ---- P2: resolve, gather depths and colors, reached bitmasks; band rows' reached
     // pixels and hole mask leave
-    resolve_window<NT, ZT>(f, depth, color, nr, y0, y1, s);
+    resolve_window<NT, ZT, WIDE>(f, depth, color, nr, y0, y1, s);
     __syncthreads();
 
     fill_band<NT, VAR>(f, y0, y1, s, ctr, rowinfo);
@@ -794,7 +810,7 @@ __device__ __forceinline__ Window window_layout(unsigned char* smem, int slots, 
     return s;
 }
 
-template <int NT, int MINB, bool VAR, bool ZT = false>
+template <int NT, int MINB, bool VAR, bool ZT = false, bool WIDE = false>
 __global__ void __launch_bounds__(NT, MINB) fused_single(FrameArgs f, int wpad)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -803,11 +819,11 @@ __global__ void __launch_bounds__(NT, MINB) fused_single(FrameArgs f, int wpad)
     const int nbands = (f.h + f.band - 1) / f.band;
     for (int b = blockIdx.x; b < nbands; b += gridDim.x) {
         const int y0 = b * f.band;
-        run_band<NT, VAR, ZT>(f, y0, min(y0 + f.band, f.h), s, ctr, rowinfo);
+        run_band<NT, VAR, ZT, WIDE>(f, y0, min(y0 + f.band, f.h), s, ctr, rowinfo);
     }
 }
 
-template <int NT, int MINB, bool ZT = false>
+template <int NT, int MINB, bool ZT = false, bool WIDE = false>
 __global__ void __launch_bounds__(NT, MINB) fused_batch(const __grid_constant__ BatchArgs a, int wpad)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -824,7 +840,7 @@ __global__ void __launch_bounds__(NT, MINB) fused_batch(const __grid_constant__ 
         // shared memory sized for max_band rows of the widest
         const Window s = window_layout(smem_raw, f.band + 2, (f.w + 7) / 8 * 8, f.w, ctr, rowinfo);
         const int y0 = (item - a.item_start[lo]) * f.band;
-        run_band<NT, false, ZT>(f, y0, min(y0 + f.band, f.h), s, ctr, rowinfo);
+        run_band<NT, false, ZT, WIDE>(f, y0, min(y0 + f.band, f.h), s, ctr, rowinfo);
     }
 }
 
@@ -1148,6 +1164,8 @@ cudaError_t fused_configure(int device, FusedLimits* lim)
                          (const void*)fused_single<kBig, 1, false, true>, (const void*)fused_single<kSmall, 2, false, true>,
                          (const void*)fused_batch<kBig, 1>,         (const void*)fused_batch<kSmall, 2>,
                          (const void*)fused_batch<kBig, 1, true>,   (const void*)fused_batch<kSmall, 2, true>,
+                         (const void*)fused_single<kBig, 1, false, false, true>,
+                         (const void*)fused_batch<kBig, 1, false, true>,
                          (const void*)fill_only<kBig, false>,       (const void*)fill_only<kBig, true>,
                          (const void*)fill_keys<kBig, false>,       (const void*)fill_keys<kBig, true>,
                          (const void*)imb_band<kBig>};
@@ -1205,6 +1223,8 @@ cudaError_t fused_launch(const FrameArgs& f, const FusedLimits& lim, int two_per
     } else {
         if (f.zt_out) fused_single<kBig, 1, false, true><<<grid, kBig, smem, stream>>>(f, wpad);
         else if (var) fused_single<kBig, 1, true><<<grid, kBig, smem, stream>>>(f, wpad);
+        else if ((f.w + 31) / 32 > 2 * (kBig / 32))  // wider than 2 words per warp
+            fused_single<kBig, 1, false, false, true><<<grid, kBig, smem, stream>>>(f, wpad);
         else fused_single<kBig, 1, false><<<grid, kBig, smem, stream>>>(f, wpad);
     }
     return cudaGetLastError();
@@ -1225,6 +1245,8 @@ cudaError_t fused_launch_batch(const BatchArgs& a, int wmax, const FusedLimits& 
         else fused_batch<kSmall, 2><<<grid, kSmall, smem, stream>>>(a, wpad);
     } else {
         if (zt) fused_batch<kBig, 1, true><<<grid, kBig, smem, stream>>>(a, wpad);
+        else if ((wmax + 31) / 32 > 2 * (kBig / 32))  // a frame wider than 2 words per warp
+            fused_batch<kBig, 1, false, true><<<grid, kBig, smem, stream>>>(a, wpad);
         else fused_batch<kBig, 1><<<grid, kBig, smem, stream>>>(a, wpad);
     }
     return cudaGetLastError();
