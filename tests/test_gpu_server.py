@@ -84,8 +84,7 @@ def test_frames_alone_and_in_the_mix_are_identical(srv):
     assert max(r.batch_frames for r in done) > 1  # frames of several streams shared launches
     _, _, co, mo = s2.slot(ids[1], 1)
     assert np.array_equal(co.cpu().numpy(), alone[0]) and np.array_equal(mo.cpu().numpy(), alone[1])
-    for sid, rnd in [(ids[0], 0), (ids[2], 2), (ids[6], 1)]:  # a few others against the oracle
-        fcfg, fc, fd = frames[(sid, rnd)]
+    for (sid, rnd), (fcfg, fc, fd) in frames.items():  # every frame of the mix against the oracle
         fc_ = fcfg.camera()
         r = oracle.synthesize(fc, fd, fc_["fx"], fc_["fy"], fc_["cx"], fc_["cy"], fc_["ipd"], fc_["near"], fc_["far"])
         _, _, co, mo = s2.slot(sid, rnd)
